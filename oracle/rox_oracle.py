@@ -1,0 +1,222 @@
+"""FP64 oracle: line strength, widths, Voigt profile and the truncated line sum.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py). Plain NumPy/SciPy in float64.
+
+Paper: pyROX (de Regt et al.), section "Functionality of pyROX":
+  * "Compute line-strengths and -widths": strength and broadening widths of every
+    transition at the user's pressure and temperature. The paper prints no formula;
+    the readings below are the standard HITRAN and ExoMol definitions.
+  * "Compute line profiles": Voigt profile = real part of the Faddeeva function
+    (Gandhi et al. 2020, Eq. 12), computed with scipy.special.wofz. That routine is
+    the one used here.
+  * "Combine and save": profiles summed into a cross-section per (P,T).
+Readings where the paper is silent (all listed in the design doc as well):
+  R1  constants CODATA 2018; T_ref = 296 K; pressures in bar, P_ref = 1 atm = 1.01325 bar.
+  R2  HITRAN strength  S(T) = S_ref * Q(T_ref)/Q(T) * exp(-c2 E''(1/T - 1/T_ref))
+                             * (1 - exp(-c2 nu0/T)) / (1 - exp(-c2 nu0/T_ref)).
+      ExoMol strength  S(T) = g_up A / (8 pi c nu0^2) * exp(-c2 E''/T) * (1 - exp(-c2 nu0/T)) / Q(T).
+      Units cm/molecule (nu0 in cm^-1, c in cm/s).
+  R3  Doppler 1/e half-width gamma_G = (nu0/c) sqrt(2 k_B T / (m amu)); HWHM = gamma_G sqrt(ln 2).
+  R4  Lorentz HWHM gamma_L = gamma_ref (T_ref/T)^n_T (P / P_ref).
+  R5  Voigt V(dnu) = Re w((dnu + i gamma_L)/gamma_G) / (gamma_G sqrt(pi)), unit area over dnu.
+  R6  Hard wing cutoff, inclusive: a line contributes to grid point j iff
+      |nu_j - nu0| <= cutoff, evaluated in float64 as abs((nu_min + j*dnu) - nu0) <= cutoff.
+      No renormalisation, no subtraction of the profile value at the cutoff.
+  R7  Point sampling at grid nodes nu_j = nu_min + j*dnu, j = 0..n-1 (computed, not accumulated).
+  R8  sigma_j = sum over lines in ascending order of S_i V_ij (float64).
+  R9  Partition function: analytic Q(T) = a T^1.5, or a 1 K table interpolated linearly.
+"""
+import numpy as np
+from scipy.special import wofz
+
+__all__ = [
+    "C_LIGHT_CM", "C_LIGHT_M", "K_B", "H_PLANCK", "C2", "AMU", "T_REF", "P_REF_BAR",
+    "partition_function", "line_strength", "doppler_width", "lorentz_width",
+    "voigt_profile", "grid_nodes", "window_indices", "count_evals",
+    "xsec_bruteforce", "xsec_windowed", "xsec_points", "xsec_window", "sort_lines",
+]
+
+# R1: CODATA 2018 exact SI values where defined
+C_LIGHT_M = 2.99792458e8          # m/s
+C_LIGHT_CM = 2.99792458e10        # cm/s
+K_B = 1.380649e-23                # J/K
+H_PLANCK = 6.62607015e-34         # J s
+C2 = H_PLANCK * C_LIGHT_CM / K_B  # second radiation constant, cm K
+AMU = 1.66053906660e-27           # kg
+T_REF = 296.0                     # K
+P_REF_BAR = 1.01325               # 1 atm in bar
+
+HITRAN, EXOMOL = 0, 1
+
+
+def partition_function(q_input, T):
+    """R9. q_input is ('analytic', a) or ('table', T_K, Q)."""
+    if q_input[0] == "analytic":
+        return q_input[1] * np.power(np.asarray(T, dtype=np.float64), 1.5)
+    _, tt, qq = q_input
+    T = np.asarray(T, dtype=np.float64)
+    if np.any(T < tt[0]) or np.any(T > tt[-1]):
+        raise ValueError("temperature outside the partition-function table")
+    return np.interp(T, tt, qq)
+
+
+def line_strength(lines, T, Q_T, Q_ref):
+    """R2. Strength S(T) in cm/molecule for every line, float64."""
+    nu0 = np.asarray(lines["nu0"], dtype=np.float64)
+    el = np.asarray(lines["e_lower"], dtype=np.float64)
+    s = np.asarray(lines["s_or_a"], dtype=np.float64)
+    stim_T = -np.expm1(-C2 * nu0 / T)       # 1 - exp(-c2 nu0 / T)
+    if lines["convention"] == HITRAN:
+        stim_ref = -np.expm1(-C2 * nu0 / T_REF)
+        boltz = np.exp(-C2 * el * (1.0 / T - 1.0 / T_REF))
+        return s * (Q_ref / Q_T) * boltz * (stim_T / stim_ref)
+    g = np.asarray(lines["g_up"], dtype=np.float64)
+    pref = g * s / (8.0 * np.pi * C_LIGHT_CM * nu0 * nu0)
+    return pref * np.exp(-C2 * el / T) * stim_T / Q_T
+
+
+def doppler_width(nu0, T, mass_amu):
+    """R3. 1/e Doppler half-width gamma_G (cm^-1)."""
+    nu0 = np.asarray(nu0, dtype=np.float64)
+    return nu0 / C_LIGHT_M * np.sqrt(2.0 * K_B * T / (mass_amu * AMU))
+
+
+def lorentz_width(gamma_ref, n_t, P_bar, T):
+    """R4. Lorentz HWHM gamma_L (cm^-1)."""
+    g = np.asarray(gamma_ref, dtype=np.float64)
+    n = np.asarray(n_t, dtype=np.float64)
+    return g * np.power(T_REF / T, n) * (P_bar / P_REF_BAR)
+
+
+def voigt_profile(dnu, gamma_G, gamma_L):
+    """R5. Area-normalised Voigt profile (cm) via scipy.special.wofz."""
+    z = (np.asarray(dnu, dtype=np.float64) + 1j * np.asarray(gamma_L, dtype=np.float64)) / gamma_G
+    return wofz(z).real / (gamma_G * np.sqrt(np.pi))
+
+
+def grid_nodes(nu_min, dnu, n, j=None):
+    """R7. nu_j = nu_min + j*dnu in float64 (one multiply, one add, no accumulation)."""
+    if j is None:
+        j = np.arange(n, dtype=np.float64)
+    return nu_min + np.asarray(j, dtype=np.float64) * dnu
+
+
+def _inside(nu_min, dnu, j, nu0, cutoff):
+    """R6 predicate for integer index arrays j (float64 arithmetic, as written)."""
+    return np.abs(grid_nodes(nu_min, dnu, None, j) - nu0) <= cutoff
+
+
+def window_indices(nu0, nu_min, dnu, n, cutoff):
+    """Per line, the first and last grid index (unclipped) satisfying R6.
+
+    With d_j = (nu_min + j*dnu) - nu0 in float64, R6 reads -cutoff <= d_j <= cutoff.
+    d_j is non-decreasing in j, so jlo is the first j with d_j >= -cutoff and jhi
+    the last j with d_j <= cutoff. A candidate from one division is moved until
+    these two tests themselves hold at the ends and fail just outside.
+    Returns (jlo, jhi) int64 arrays; jlo > jhi means the line touches no node.
+    """
+    nu0 = np.asarray(nu0, dtype=np.float64)
+
+    def d(j):
+        return grid_nodes(nu_min, dnu, None, j) - nu0
+
+    jlo = np.ceil((nu0 - cutoff - nu_min) / dnu).astype(np.int64)
+    jhi = np.floor((nu0 + cutoff - nu_min) / dnu).astype(np.int64)
+    for _ in range(8):
+        jlo = np.where(d(jlo - 1) >= -cutoff, jlo - 1, jlo)
+        jlo = np.where(d(jlo) < -cutoff, jlo + 1, jlo)
+        jhi = np.where(d(jhi + 1) <= cutoff, jhi + 1, jhi)
+        jhi = np.where(d(jhi) > cutoff, jhi - 1, jhi)
+    assert np.all(d(jlo) >= -cutoff) and np.all(d(jlo - 1) < -cutoff)
+    assert np.all(d(jhi) <= cutoff) and np.all(d(jhi + 1) > cutoff)
+    return jlo, jhi
+
+
+def count_evals(nu0, nu_min, dnu, n, cutoff):
+    """Number of (line, grid node) pairs inside the cutoff (the unit of work)."""
+    jlo, jhi = window_indices(nu0, nu_min, dnu, n, cutoff)
+    lo = np.maximum(jlo, 0)
+    hi = np.minimum(jhi, n - 1)
+    return int(np.sum(np.maximum(hi - lo + 1, 0)))
+
+
+def sort_lines(lines):
+    """Lines in ascending nu0 (stable, so equal nu0 keep generation order)."""
+    order = np.argsort(np.asarray(lines["nu0"]), kind="stable")
+    out = {}
+    for k, v in lines.items():
+        out[k] = v[order] if isinstance(v, np.ndarray) else v
+    return out
+
+
+def _line_params(lines, P_bar, T, Q_T, Q_ref, mass_amu):
+    S = line_strength(lines, T, Q_T, Q_ref)
+    gG = doppler_width(lines["nu0"], T, mass_amu)
+    gL = lorentz_width(lines["gamma_ref"], lines["n_t"], P_bar, T)
+    return S, gG, gL
+
+
+def xsec_bruteforce(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff):
+    """R8 by brute force: every line against every node, explicit R6 test,
+    lines added in the order given. For tiny inputs only (O(lines x nodes))."""
+    nu_min, dnu, n = grid
+    nu = grid_nodes(nu_min, dnu, n)
+    S, gG, gL = _line_params(lines, P_bar, T, Q_T, Q_ref, mass_amu)
+    sigma = np.zeros(n, dtype=np.float64)
+    nu0 = np.asarray(lines["nu0"], dtype=np.float64)
+    for i in range(nu0.size):
+        d = nu - nu0[i]
+        contrib = S[i] * voigt_profile(d, gG[i], gL[i])
+        sigma += np.where(np.abs(d) <= cutoff, contrib, 0.0)
+    return sigma
+
+
+def xsec_windowed(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff):
+    """R8, each line touching only its own cutoff window (same order as brute force,
+    so the two agree bit for bit: the brute force adds +0.0 elsewhere)."""
+    nu_min, dnu, n = grid
+    S, gG, gL = _line_params(lines, P_bar, T, Q_T, Q_ref, mass_amu)
+    nu0 = np.asarray(lines["nu0"], dtype=np.float64)
+    jlo, jhi = window_indices(nu0, nu_min, dnu, n, cutoff)
+    sigma = np.zeros(n, dtype=np.float64)
+    for i in range(nu0.size):
+        a, b = max(int(jlo[i]), 0), min(int(jhi[i]), n - 1)
+        if a > b:
+            continue
+        j = np.arange(a, b + 1)
+        d = grid_nodes(nu_min, dnu, n, j) - nu0[i]
+        sigma[a:b + 1] += S[i] * voigt_profile(d, gG[i], gL[i])
+    return sigma
+
+
+def xsec_window(lines_sorted, grid, j0, j1, P_bar, T, Q_T, Q_ref, mass_amu, cutoff):
+    """sigma at nodes j0..j1-1 exactly (R8), from lines sorted by nu0.
+
+    Only lines with nu0 within cutoff of the window can contribute (R6), so the
+    candidate set is cut from the sorted list with a margin and the R6 predicate
+    then decides each pair. Lines are added in ascending sorted order, so the
+    result equals the full-grid sum at those nodes bit for bit."""
+    nu_min, dnu, n = grid
+    nu0 = np.asarray(lines_sorted["nu0"], dtype=np.float64)
+    lo_nu = grid_nodes(nu_min, dnu, n, j0) - cutoff - 4 * dnu
+    hi_nu = grid_nodes(nu_min, dnu, n, j1 - 1) + cutoff + 4 * dnu
+    a = int(np.searchsorted(nu0, lo_nu, side="left"))
+    b = int(np.searchsorted(nu0, hi_nu, side="right"))
+    sub = {k: (v[a:b] if isinstance(v, np.ndarray) else v) for k, v in lines_sorted.items()}
+    S, gG, gL = _line_params(sub, P_bar, T, Q_T, Q_ref, mass_amu)
+    nu = grid_nodes(nu_min, dnu, n, np.arange(j0, j1))
+    sigma = np.zeros(j1 - j0, dtype=np.float64)
+    for i in range(b - a):
+        d = nu - sub["nu0"][i]
+        m = np.abs(d) <= cutoff
+        if m.any():
+            sigma[m] += S[i] * voigt_profile(d[m], gG[i], gL[i])
+    return sigma
+
+
+def xsec_points(lines_sorted, grid, js, P_bar, T, Q_T, Q_ref, mass_amu, cutoff):
+    """sigma at the listed nodes js, one node at a time (exact, same order as R8)."""
+    out = np.empty(len(js), dtype=np.float64)
+    for k, j in enumerate(js):
+        out[k] = xsec_window(lines_sorted, grid, int(j), int(j) + 1, P_bar, T, Q_T, Q_ref, mass_amu, cutoff)[0]
+    return out
