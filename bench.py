@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of the line-by-line opacity cross-section hot path on GB300.
+
+Workload (default): the ExoMol-style single-(P,T) case -- 1e7 synthetic lines, nu0 uniform
+300-30000 cm^-1, grid 300-30000 cm^-1 at 0.01 cm^-1 (2,970,001 points), 25 cm^-1 wing
+cutoff, (P,T) = (0.1 bar, 1500 K). One step = one cross-section through the C ABI
+(rox_xsec) on the resident, nu0-sorted line list: line strengths and widths, windows and
+tile ranges, Voigt evaluation and accumulation. Metric: Voigt line-profile evaluations per
+second, one evaluation being a (line, grid point) pair inside the cutoff, counted exactly.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rox|reference]
+
+--impl reference times the FP64 CPU oracle (scipy.special.wofz) on a bounded sample of
+the same workload on the host cores. Under torchrun (N > 1) every rank runs one replica
+of the workload on its own GPU (the path has no exchange step).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import rox_synth as rs  # noqa: E402
+
+FLOPS_PER_EVAL = 11.0   # far-wing pair formula: 10 FFMA + 2 FMUL per 2 evaluations (+ 1 MUFU rcp)
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+METRIC = "Voigt line-profile evals/s"
+UNIT = "evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rox", choices=["rox", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(cid):
+    w = rs.CONFIGS[cid]
+    grid = rs.grid_of(w)
+    (P, T), = w.pts
+    q = rs.q_table(w)
+    return w, grid, P, T, q
+
+
+def q_of(q, T):
+    """Q(T) for the GPU arm (the library's host-side helper)."""
+    from paper_2510_20870_gb300.partition import PartitionFunction
+    return PartitionFunction(q)(T)
+
+
+def q_oracle(q, T):
+    """Q(T) for the CPU oracle arm."""
+    import oracle
+    return float(oracle.partition_function(q, T))
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline / reference arm)
+def _oracle_window(args):
+    sub, grid, j0, j1, P, T, Qt, Qr, mass, cutoff = args
+    import oracle
+    s = oracle.xsec_window(sub, grid, j0, j1, P, T, Qt, Qr, mass, cutoff)
+    jlo, jhi = oracle.window_indices(sub["nu0"], *grid, cutoff)
+    ev = int(np.sum(np.maximum(np.minimum(jhi, j1 - 1) - np.maximum(jlo, j0) + 1, 0)))
+    return ev, float(s.sum())
+
+
+def oracle_sample_tasks(Ls, grid, P, T, Qt, Qr, mass, cutoff, n_windows, width, seed):
+    rng = np.random.default_rng(seed)
+    tasks = []
+    nu0 = Ls["nu0"]
+    for s in rng.integers(0, grid[2] - width, n_windows):
+        lo = grid[0] + grid[1] * s - cutoff - 1.0
+        hi = grid[0] + grid[1] * (s + width) + cutoff + 1.0
+        a, b = np.searchsorted(nu0, lo), np.searchsorted(nu0, hi)
+        sub = {k: (v[a:b] if isinstance(v, np.ndarray) else v) for k, v in Ls.items()}
+        tasks.append((sub, grid, int(s), int(s) + width, P, T, Qt, Qr, mass, cutoff))
+    return tasks
+
+
+def time_oracle(tasks, cores):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_window, tasks[:cores])          # warm the workers (imports)
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_window, tasks, chunksize=1)
+        dt = time.perf_counter() - t0
+    return sum(r[0] for r in res), dt
+
+
+def sorted_host_lines(w):
+    import oracle
+    return oracle.sort_lines(rs.make_lines(w))
+
+
+def cpu_baseline(w, grid, P, T, q, Ls, target_s):
+    cores = len(os.sched_getaffinity(0))
+    Qt, Qr = q_oracle(q, T), q_oracle(q, 296.0)
+    width = 256
+    probe = oracle_sample_tasks(Ls, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, cores, width, 7)
+    ev, dt = time_oracle(probe, cores)
+    rate = ev / dt
+    n_win = max(cores, int(target_s * rate / (ev / len(probe))))
+    tasks = oracle_sample_tasks(Ls, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, n_win, width, 8)
+    ev, dt = time_oracle(tasks, cores)
+    return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d random windows of %d grid points of the %s workload (all lines within the cutoff "
+                      "of each window), FP64 scipy.special.wofz, %d evals in %.1f s" % (n_win, width, w.name, ev, dt)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, grid, P, T, q = workload(args.config)
+    Ls = sorted_host_lines(w)
+    cores = len(os.sched_getaffinity(0))
+    Qt, Qr = q_oracle(q, T), q_oracle(q, 296.0)
+    per_step = 2 * cores
+    rates, total_ev, total_t = [], 0, 0.0
+    for step in range(args.warmup + args.steps):
+        tasks = oracle_sample_tasks(Ls, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, per_step, 256, 100 + step)
+        ev, dt = time_oracle(tasks, cores)
+        if step >= args.warmup:
+            total_ev += ev
+            total_t += dt
+    value = total_ev / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s: %d lines, grid %d points, cutoff %g cm^-1, (P,T)=(%g bar, %g K)" % (
+                w.name, w.n_lines, grid[2], w.cutoff, P, T), "sample_per_step": "%d windows x 256 points" % per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d steps of %d random 256-point windows, FP64 scipy.special.wofz" % (
+                                 args.steps, per_step)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args):
+    import torch
+    import paper_2510_20870_gb300 as rox
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    w, grid, P, T, q = workload(args.config)
+    Qt, Qr = q_of(q, T), q_of(q, 296.0)
+    host = rs.make_lines(w)                   # unsorted, generation order
+    cols = ["nu0", "s_or_a", "g_up", "e_lower", "gamma_ref", "n_t"]
+    pinned = {k: torch.from_numpy(host[k]).pin_memory() for k in cols if host[k] is not None}
+    raw = {k: torch.empty_like(v, device=dev) for k, v in pinned.items()}
+    raw["convention"] = host["convention"]
+    lines = {k: torch.empty_like(v) for k, v in raw.items() if k != "convention"}
+    lines["convention"] = host["convention"]
+    raw.setdefault("g_up", None)
+    lines.setdefault("g_up", None)
+    n = len(host["nu0"])
+    h2d_bytes = sum(v.numel() * v.element_size() for v in pinned.values())
+    sort_ws = torch.empty(rox.rox_sort_workspace_size(n), dtype=torch.uint8, device=dev)
+    ws = torch.empty(rox.rox_xsec_workspace_size(n, grid, 1), dtype=torch.uint8, device=dev)
+    sigma = torch.empty((1, grid[2]), dtype=torch.float32, device=dev)
+    sigma_host = torch.empty((1, grid[2]), dtype=torch.float32).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def upload_and_sort():
+        for k, v in pinned.items():
+            raw[k].copy_(v, non_blocking=True)
+        rox.rox_sort_lines(raw, lines, None, sort_ws)
+
+    def step():
+        rox.rox_xsec(lines, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
+
+    upload_and_sort()
+    step()
+    rc, evals = rox.rox_ws_status(ws)
+    if rc != 0:
+        raise RuntimeError(rox.lib.rox_last_error().decode())
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput, with the Voigt kernel timed by events around its launch
+    for _ in range(args.warmup):
+        step()
+    ev_pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev_pairs:
+        a.record()
+        b.record()
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        time.sleep(0.3)
+        barrier()
+        t0.record()
+        for a, b in ev_pairs:
+            rox.rox_set_profile_events(a, b)
+            step()
+        rox.rox_set_profile_events(None, None)
+        t1.record()
+        barrier()
+    ms = t0.elapsed_time(t1)
+    voigt_ms = [a.elapsed_time(b) for a, b in ev_pairs]
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_per_step = ms / args.steps
+    value = world * evals * args.steps / (ms * 1e-3)
+
+    # ---- end to end through the public API: pinned host -> device, sort, xsec, sigma -> host
+    for _ in range(max(1, args.warmup // 2)):
+        upload_and_sort()
+        step()
+        sigma_host.copy_(sigma, non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        upload_and_sort()
+        step()
+        sigma_host.copy_(sigma, non_blocking=True)
+    e1.record()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = world * evals * args.steps / (e2e_ms * 1e-3)
+    assert np.isfinite(sigma_host.numpy()).all()
+
+    csum = clocks.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    v_ms = statistics.mean(voigt_ms)
+    achieved = evals * FLOPS_PER_EVAL / (v_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_voigt", "kernel_ms": v_ms,
+            "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, SM_MAX_MHZ),
+            "flops_per_eval": FLOPS_PER_EVAL}
+    if csum.get("sm_mhz"):
+        roof["frac_at_median_clock"] = achieved / (sms * FP32_LANES_PER_SM * 2 * csum["sm_mhz"] * 1e6 / 1e12)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        Ls = oracle.sort_lines(host)
+        cpu = cpu_baseline(w, grid, P, T, q, Ls, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "%s: %d lines (ExoMol-style), grid %g-%g cm^-1 at %g (%d points), cutoff %g "
+                           "cm^-1, (P,T)=(%g bar, %g K)" % (w.name, w.n_lines, w.grid_lo, w.grid_hi, w.dnu, grid[2],
+                                                           w.cutoff, P, T),
+                           "evals_per_step": evals, "xsecs_per_s": world * args.steps / (ms * 1e-3),
+                           "step": "rox_xsec on the resident nu0-sorted list (strengths, widths, windows, tile "
+                                   "ranges, Voigt accumulate); the once-per-list sort is inside e2e",
+                           "l2": "inputs larger than L2 (line list %.0f MB, workspace %.0f MB)" % (
+                               h2d_bytes / 1e6, ws.numel() / 1e6),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+                        "d2h_bytes_per_step": sigma.numel() * 4, "ms_per_step": e2e_ms / args.steps,
+                        "includes": "H2D of the unsorted list, rox_sort_lines, rox_xsec, D2H of sigma"},
+                "gpu_launches": args.steps * 4,
+                "gpu_launches_note": "per step: windows, strengths, tile ranges, Voigt kernels (+1 memset)",
+                "clocks": csum}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/* rox.h -- C ABI of librox: line-by-line opacity cross-sections on a GB300 (sm_103a).
+ *
+ * The method is that of the pyROX paper (de Regt, Gandhi, Siebenaler, Gonzalez Picos),
+ * section "Functionality of pyROX":
+ *   - "Compute line-strengths and -widths": every transition gets a strength and
+ *     broadening widths at the requested pressure and temperature;
+ *   - "Compute line profiles": a Voigt profile, the real part of the Faddeeva
+ *     function (Gandhi et al. 2020, Eq. 12);
+ *   - "Combine and save": the profiles are summed into a cross-section sigma(nu)
+ *     for each temperature-pressure point.
+ * The paper prints no formula. The definitions used (standard HITRAN / ExoMol forms) are:
+ *   S(T) HITRAN = S_ref Q(296)/Q(T) exp(-c2 E''(1/T - 1/296)) (1 - e^{-c2 nu0/T})/(1 - e^{-c2 nu0/296})
+ *   S(T) ExoMol = g_up A / (8 pi c nu0^2) exp(-c2 E''/T) (1 - e^{-c2 nu0/T}) / Q(T)
+ *   gamma_G     = (nu0/c) sqrt(2 k_B T / (m amu))            (1/e Doppler half-width)
+ *   gamma_L     = gamma_ref (296/T)^n_T (P / 1.01325 bar)      (Lorentz HWHM)
+ *   V(dnu)      = Re w((dnu + i gamma_L)/gamma_G) / (gamma_G sqrt(pi))
+ *   sigma_j     = sum over lines with |nu_j - nu0| <= cutoff of S V(nu_j - nu0),
+ *                 nu_j = nu_min + j dnu, the cutoff test taken in double precision exactly
+ *                 as written (inclusive, no renormalisation).
+ * Units: wavenumbers cm^-1, T in K, P in bar, S in cm/molecule, sigma in cm^2/molecule.
+ *
+ * Conventions for every call:
+ *   - returns ROX_OK (0) or an error code below; rox_last_error() gives a message
+ *     (thread-local). On an argument error nothing is launched and no output is written.
+ *   - array pointers are DEVICE pointers owned by the caller unless stated otherwise;
+ *     scalars and small per-point arrays marked "host" are host memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). All work is enqueued on
+ *     it asynchronously; no call synchronises unless its comment says so.
+ *   - scratch memory is a caller-provided device workspace `ws` of `ws_bytes` bytes
+ *     (256-byte aligned); the library allocates nothing on the hot path.
+ *   - errors found on the device (unsorted input, a bounded wait running out) are
+ *     recorded in the workspace and returned by rox_ws_status().
+ */
+#ifndef ROX_H
+#define ROX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ROX_OK 0
+#define ROX_EINVAL 1      /* invalid argument: null pointer, n <= 0, T <= 0, P < 0, Q <= 0, ... */
+#define ROX_ENOMEM 2      /* workspace smaller than the matching *_workspace_size() */
+#define ROX_ECUDA 3       /* a CUDA runtime call failed (see rox_last_error) */
+#define ROX_ETIMEOUT 4    /* a bounded device-side wait ran out (reported by rox_ws_status) */
+#define ROX_EUNSORTED 5   /* line list not in ascending nu0 (reported by rox_ws_status) */
+#define ROX_ERANGE 6      /* a size beyond a documented limit */
+
+/* line-list conventions */
+#define ROX_HITRAN 0      /* s_or_a = S_ref at 296 K (cm/molecule) */
+#define ROX_EXOMOL 1      /* s_or_a = Einstein A (s^-1), g_up required */
+
+/* storage type of the gamma_ref / n_t columns */
+#define ROX_WIDTH_F32 0
+#define ROX_WIDTH_F16 1
+
+/* flags of rox_xsec_batch */
+#define ROX_ACCUMULATE 1u /* add into sigma_out instead of overwriting it (chunked line lists) */
+
+/* limits */
+#define ROX_MAX_PT 512            /* (P,T) points per rox_xsec_batch call */
+#define ROX_MAX_GRID (1 << 23)    /* grid points (line-centre indices are carried exactly in FP32) */
+#define ROX_MAX_CUTOFF_STEPS (1 << 21) /* cutoff / dnu */
+
+/* A line list as structure-of-arrays, n lines, all DEVICE pointers.
+ * nu0       [n] double  line centre (cm^-1), > 0
+ * s_or_a    [n] float   HITRAN: S_ref at 296 K (cm/molecule); ExoMol: Einstein A (s^-1)
+ * g_up      [n] float   ExoMol upper-state degeneracy (ignored and may be NULL for HITRAN)
+ * e_lower   [n] float   lower-state energy E'' (cm^-1)
+ * gamma_ref [n] float|half  Lorentz HWHM at 296 K and 1 atm (cm^-1 atm^-1)
+ * n_t       [n] float|half  temperature exponent of gamma_L
+ * The cross-section calls need the list sorted by ascending nu0 (rox_sort_lines). */
+typedef struct rox_lines {
+  const double* nu0;
+  const float* s_or_a;
+  const float* g_up;
+  const float* e_lower;
+  const void* gamma_ref;
+  const void* n_t;
+  int64_t n;
+  int32_t convention;   /* ROX_HITRAN or ROX_EXOMOL */
+  int32_t width_dtype;  /* ROX_WIDTH_F32 or ROX_WIDTH_F16 */
+} rox_lines;
+
+/* Writable twin of rox_lines (outputs of rox_sort_lines). */
+typedef struct rox_lines_buf {
+  double* nu0;
+  float* s_or_a;
+  float* g_up;
+  float* e_lower;
+  void* gamma_ref;
+  void* n_t;
+} rox_lines_buf;
+
+/* Uniform wavenumber grid nu_j = nu_min + j*dnu, j = 0..n-1 (cm^-1). */
+typedef struct rox_grid {
+  double nu_min;
+  double dnu;
+  int64_t n;
+} rox_grid;
+
+/* Message of the last error on this thread ("" if none). Never NULL. */
+const char* rox_last_error(void);
+/* Library version string. */
+const char* rox_version(void);
+
+/* a1 -- line strengths S(T) (cm/molecule) of all lines, FP32 output, FP64 arithmetic
+ * for the Boltzmann and stimulated-emission factors and the partition-function ratio.
+ * Paper: "Compute line-strengths and -widths".
+ * T > 0 (K); Q_T = Q(T) > 0 and Q_ref = Q(296 K) > 0 are computed by the caller (host).
+ * S_out [n] float (device). Strengths below the FP32 range round to 0 or a subnormal. */
+int rox_line_strengths(const rox_lines* lines, double T, double Q_T, double Q_ref,
+                       float* S_out, void* stream);
+
+/* a2 -- Doppler 1/e half-widths gamma_G and Lorentz HWHM gamma_L (cm^-1), FP32 outputs.
+ * Paper: "Compute line-strengths and -widths" (pressure broadening: single power law).
+ * mass_amu > 0, P_bar >= 0, T > 0. gamma_G_out, gamma_L_out [n] float (device). */
+int rox_line_widths(const rox_lines* lines, double mass_amu, double P_bar, double T,
+                    float* gamma_G_out, float* gamma_L_out, void* stream);
+
+/* a3 (sort) -- copy of the line list in ascending nu0 (stable: equal nu0 keep input
+ * order) into `out` (device buffers of n elements; g_up may be NULL for HITRAN), and the
+ * permutation perm_out[k] = input index of output line k (int64, device, may be NULL).
+ * Workspace: rox_sort_workspace_size(n). */
+size_t rox_sort_workspace_size(int64_t n);
+int rox_sort_lines(const rox_lines* in, const rox_lines_buf* out, int64_t* perm_out,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* a3 (binning) -- per sorted line, the grid-index window and centre decomposition:
+ *   jlo[i], jhi[i]: first and last grid index j with |nu_j - nu0_i| <= cutoff, the test
+ *                   evaluated in double precision as abs((nu_min + j*dnu) - nu0) <= cutoff;
+ *                   jlo clamped to [0, n], jhi to [-1, n-1]; jlo > jhi when no grid point
+ *                   is in range (both are non-decreasing along a sorted list);
+ *   k0[i], f[i]:    (nu0 - nu_min)/dnu = k0 + f with k0 integer and f in [0, 1).
+ * evals_out (device, 1 x uint64): number of (line, grid point) pairs inside the cutoff,
+ * added to the value already there. unsorted_out (device, 1 x int32): set to 1 if nu0 is
+ * not ascending (left unchanged otherwise). Any output pointer may be NULL. */
+int rox_line_windows(const double* nu0_sorted, int64_t n_lines, const rox_grid* grid,
+                     double cutoff, int32_t* jlo, int32_t* jhi, int32_t* k0, float* f,
+                     unsigned long long* evals_out, int32_t* unsorted_out, void* stream);
+
+/* a3 (prefix) -- per wavenumber tile t (tile_pts grid points, tile t covers grid indices
+ * [t*tile_pts, (t+1)*tile_pts)), the range [lo[t], hi[t]) of sorted lines whose window
+ * [jlo, jhi] meets the tile. Equivalent to the exclusive prefix sum of the per-tile line
+ * histogram; read off the sorted order without atomics. lo_out, hi_out: n_tiles int64. */
+int rox_tile_ranges(const int32_t* jlo, const int32_t* jhi, int64_t n_lines, int64_t n_grid,
+                    int32_t tile_pts, int64_t* lo_out, int64_t* hi_out, void* stream);
+
+/* FP32 Faddeeva real part used by the Voigt kernel: out[i] = Re w(x[i] + i y[i]), y >= 0.
+ * All device arrays of n floats. Max relative error against an FP64 reference about 1.1e-5
+ * (values below 1e-15 excepted). */
+int rox_faddeeva_re(const float* x, const float* y, float* out, int64_t n, void* stream);
+
+/* a4/a5 -- cross-sections at n_pt (P,T) points in one persistent launch.
+ * lines     sorted line list (device)
+ * grid      output grid (host struct); n <= ROX_MAX_GRID
+ * P_bar, T, Q_T   [n_pt] HOST arrays: pressure (bar, >= 0), temperature (K, > 0),
+ *                 partition function Q(T) (> 0); Q_ref = Q(296 K) (> 0)
+ * mass_amu  molecular mass (> 0); cutoff  wing cutoff (cm^-1, > 0), cutoff/dnu <= ROX_MAX_CUTOFF_STEPS
+ * flags     0 or ROX_ACCUMULATE
+ * sigma_out [n_pt][grid->n] float (device), point-major; each grid point is written once
+ *           per call with a fixed summation order (bitwise reproducible run to run).
+ * ws        device workspace of rox_xsec_workspace_size(lines->n, grid, n_temps) bytes, where
+ *           n_temps is the number of distinct temperatures among T[0..n_pt-1] (S(T) is
+ *           computed once per distinct temperature and kept in the workspace in FP64).
+ * Voigt profile and tile sums in FP32 (compensated across line chunks); FP64 for the
+ * Boltzmann / stimulated-emission factors, partition ratio and line-centre offsets. */
+size_t rox_xsec_workspace_size(int64_t n_lines, const rox_grid* grid, int n_temps);
+int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt,
+                   const double* P_bar, const double* T, const double* Q_T, double Q_ref,
+                   double mass_amu, double cutoff, unsigned flags, float* sigma_out,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* a4 -- one (P,T) point: rox_xsec_batch with n_pt = 1 and flags = 0. */
+int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double T,
+             double Q_T, double Q_ref, double mass_amu, double cutoff, float* sigma_out,
+             void* ws, size_t ws_bytes, void* stream);
+
+/* Synchronises `stream` and returns the device-side status recorded in `ws` by the last
+ * rox_xsec / rox_xsec_batch call that used it: ROX_OK, ROX_EUNSORTED (lines not in
+ * ascending nu0: no sigma was written), or ROX_ETIMEOUT. If evals_out is not NULL it
+ * receives the number of (line, grid point) pairs inside the cutoff summed over the
+ * call's (P,T) points (the unit of work of the Voigt kernel). */
+int rox_ws_status(const void* ws, unsigned long long* evals_out, void* stream);
+
+/* Measurement hook: when start/stop are not NULL (cudaEvent_t handles created by the
+ * caller), every following rox_xsec / rox_xsec_batch call on this thread records `start`
+ * just before and `stop` just after its Voigt-accumulate kernel launch, on the call's
+ * stream. Pass NULL, NULL to stop. Recording is stream-ordered and adds no sync. */
+int rox_set_profile_events(void* start, void* stop);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROX_H */

@@ -1,0 +1,192 @@
+"""ctypes binding of librox (include/rox.h): argument marshalling only.
+
+Every function here takes torch CUDA tensors (device memory) and host scalars, builds
+the C structs and calls the C entry point of the same name. Nothing is computed here:
+each step of the cross-section path runs in the library's CUDA kernels. A non-zero
+status raises RoxError with the library's message.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librox.so")
+
+ROX_OK, ROX_EINVAL, ROX_ENOMEM, ROX_ECUDA, ROX_ETIMEOUT, ROX_EUNSORTED, ROX_ERANGE = range(7)
+ROX_HITRAN, ROX_EXOMOL = 0, 1
+ROX_WIDTH_F32, ROX_WIDTH_F16 = 0, 1
+ROX_ACCUMULATE = 1
+ROX_MAX_PT = 512
+ROX_TILE = 2048  # grid points per CTA tile (ROX_THREADS * ROX_K)
+
+
+class RoxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("librox error %d: %s" % (code, msg))
+        self.code = code
+
+
+class RoxLines(ctypes.Structure):
+    _fields_ = [("nu0", ctypes.c_void_p), ("s_or_a", ctypes.c_void_p), ("g_up", ctypes.c_void_p),
+                ("e_lower", ctypes.c_void_p), ("gamma_ref", ctypes.c_void_p), ("n_t", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("convention", ctypes.c_int32), ("width_dtype", ctypes.c_int32)]
+
+
+class RoxLinesBuf(ctypes.Structure):
+    _fields_ = [("nu0", ctypes.c_void_p), ("s_or_a", ctypes.c_void_p), ("g_up", ctypes.c_void_p),
+                ("e_lower", ctypes.c_void_p), ("gamma_ref", ctypes.c_void_p), ("n_t", ctypes.c_void_p)]
+
+
+class RoxGrid(ctypes.Structure):
+    _fields_ = [("nu_min", ctypes.c_double), ("dnu", ctypes.c_double), ("n", ctypes.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("librox.so is not built: run `python -c \"import __graft_entry__ as g; g.build()\"` "
+                          "(or python -m paper_2510_20870_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, D, U = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint
+    sig = {
+        "rox_last_error": (ctypes.c_char_p, []),
+        "rox_version": (ctypes.c_char_p, []),
+        "rox_line_strengths": (ctypes.c_int, [P, D, D, D, P, P]),
+        "rox_line_widths": (ctypes.c_int, [P, D, D, D, P, P, P]),
+        "rox_sort_workspace_size": (ctypes.c_size_t, [I64]),
+        "rox_sort_lines": (ctypes.c_int, [P, P, P, P, ctypes.c_size_t, P]),
+        "rox_line_windows": (ctypes.c_int, [P, I64, P, D, P, P, P, P, P, P, P]),
+        "rox_tile_ranges": (ctypes.c_int, [P, P, I64, I64, I32, P, P, P]),
+        "rox_faddeeva_re": (ctypes.c_int, [P, P, P, I64, P]),
+        "rox_xsec_workspace_size": (ctypes.c_size_t, [I64, P, ctypes.c_int]),
+        "rox_xsec_batch": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P, ctypes.c_size_t, P]),
+        "rox_xsec": (ctypes.c_int, [P, P, D, D, D, D, D, D, P, P, ctypes.c_size_t, P]),
+        "rox_ws_status": (ctypes.c_int, [P, P, P]),
+        "rox_set_profile_events": (ctypes.c_int, [P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def version():
+    return lib.rox_version().decode()
+
+
+def _check(rc):
+    if rc != ROX_OK:
+        raise RoxError(rc, lib.rox_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def lines_struct(lines):
+    """rox_lines from a dict of CUDA tensors: nu0 float64, s_or_a/e_lower (g_up) float32,
+    gamma_ref/n_t float32 or float16; 'convention' 0 (HITRAN) or 1 (ExoMol)."""
+    gref = lines["gamma_ref"]
+    wd = ROX_WIDTH_F16 if gref.dtype == torch.float16 else ROX_WIDTH_F32
+    L = RoxLines(nu0=_ptr(lines["nu0"]).value, s_or_a=_ptr(lines["s_or_a"]).value,
+                 g_up=(_ptr(lines["g_up"]).value if lines.get("g_up") is not None else None),
+                 e_lower=_ptr(lines["e_lower"]).value, gamma_ref=_ptr(gref).value,
+                 n_t=_ptr(lines["n_t"]).value, n=lines["nu0"].numel(),
+                 convention=int(lines["convention"]), width_dtype=wd)
+    return L
+
+
+def grid_struct(grid):
+    nu_min, dnu, n = grid
+    return RoxGrid(float(nu_min), float(dnu), int(n))
+
+
+def rox_line_strengths(lines, T, Q_T, Q_ref, S_out, stream=None):
+    L = lines_struct(lines)
+    _check(lib.rox_line_strengths(ctypes.byref(L), T, Q_T, Q_ref, _ptr(S_out), _stream(stream)))
+
+
+def rox_line_widths(lines, mass_amu, P_bar, T, gamma_G_out, gamma_L_out, stream=None):
+    L = lines_struct(lines)
+    _check(lib.rox_line_widths(ctypes.byref(L), mass_amu, P_bar, T, _ptr(gamma_G_out), _ptr(gamma_L_out),
+                               _stream(stream)))
+
+
+def rox_sort_workspace_size(n):
+    return lib.rox_sort_workspace_size(n)
+
+
+def rox_sort_lines(lines, out, perm_out, ws, stream=None):
+    L = lines_struct(lines)
+    B = RoxLinesBuf(nu0=_ptr(out["nu0"]).value, s_or_a=_ptr(out["s_or_a"]).value,
+                    g_up=(_ptr(out["g_up"]).value if out.get("g_up") is not None else None),
+                    e_lower=_ptr(out["e_lower"]).value, gamma_ref=_ptr(out["gamma_ref"]).value,
+                    n_t=_ptr(out["n_t"]).value)
+    _check(lib.rox_sort_lines(ctypes.byref(L), ctypes.byref(B), _ptr(perm_out), _ptr(ws), ws.numel(),
+                              _stream(stream)))
+
+
+def rox_line_windows(nu0, grid, cutoff, jlo=None, jhi=None, k0=None, f=None, evals=None, unsorted=None,
+                     stream=None):
+    G = grid_struct(grid)
+    _check(lib.rox_line_windows(_ptr(nu0), nu0.numel(), ctypes.byref(G), cutoff, _ptr(jlo), _ptr(jhi), _ptr(k0),
+                                _ptr(f), _ptr(evals), _ptr(unsorted), _stream(stream)))
+
+
+def rox_tile_ranges(jlo, jhi, n_grid, tile_pts, lo_out, hi_out, stream=None):
+    _check(lib.rox_tile_ranges(_ptr(jlo), _ptr(jhi), jlo.numel(), n_grid, tile_pts, _ptr(lo_out), _ptr(hi_out),
+                               _stream(stream)))
+
+
+def rox_faddeeva_re(x, y, out, stream=None):
+    _check(lib.rox_faddeeva_re(_ptr(x), _ptr(y), _ptr(out), x.numel(), _stream(stream)))
+
+
+def rox_xsec_workspace_size(n_lines, grid, n_temps):
+    G = grid_struct(grid)
+    return lib.rox_xsec_workspace_size(n_lines, ctypes.byref(G), n_temps)
+
+
+def rox_xsec_batch(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, flags=0, stream=None):
+    n_pt = len(P_bar)
+    arr = ctypes.c_double * n_pt
+    L = lines_struct(lines)
+    G = grid_struct(grid)
+    _check(lib.rox_xsec_batch(ctypes.byref(L), ctypes.byref(G), n_pt, arr(*P_bar), arr(*T), arr(*Q_T), Q_ref,
+                              mass_amu, cutoff, flags, _ptr(sigma_out), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def rox_xsec(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, stream=None):
+    L = lines_struct(lines)
+    G = grid_struct(grid)
+    _check(lib.rox_xsec(ctypes.byref(L), ctypes.byref(G), P_bar, T, Q_T, Q_ref, mass_amu, cutoff, _ptr(sigma_out),
+                        _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def rox_set_profile_events(start=None, stop=None):
+    """start/stop: torch.cuda.Event (enable_timing=True, already recorded once so that the
+    CUDA event exists) or None to disable."""
+    h = (lambda e: None if e is None else ctypes.c_void_p(e.cuda_event))
+    _check(lib.rox_set_profile_events(h(start), h(stop)))
+
+
+def rox_ws_status(ws, stream=None):
+    """Synchronises the stream; returns (status code, evals) and does not raise."""
+    ev = ctypes.c_ulonglong(0)
+    rc = lib.rox_ws_status(_ptr(ws), ctypes.byref(ev), _stream(stream))
+    return rc, ev.value

@@ -1,0 +1,189 @@
+// FP32 real part of the Faddeeva function, Re w(x + iy) = sqrt(pi) * K(x, y), for the
+// Voigt profile V(dnu) = Re w((dnu + i gamma_L)/gamma_G) / (gamma_G sqrt(pi))
+// (pyROX paper, "Compute line profiles": Voigt profile as the real part of the
+// Faddeeva function, Gandhi et al. 2020 Eq. 12; the paper evaluates it with
+// scipy.special.wofz in double precision).
+//
+// Region split on s = x^2 + y^2 (x >= 0; Re w is even in x), each method written
+// from its published definition and checked against wofz (max relative error of
+// Re w about 1e-5 over x in [0, 1e5], y in [0, 1e4]):
+//   s >= 22^2          2-level Laplace continued fraction (Humlicek 1982, region I form)
+//   10^2 <= s < 22^2   3-level continued fraction
+//   6^2  <= s < 10^2   5-level continued fraction (+ Gaussian term for y < 1e-6)
+//   4.5^2 <= s < 6^2   8-level continued fraction + e^{y^2-x^2} cos(2xy) for y < 1
+//   s < 4.5^2, y >= 0.1  Weideman (1994) rational approximation, N = 20
+//   s < 4.5^2, y <  0.1  Re w = e^{y^2-x^2} cos(2xy) - (2/sqrt(pi)) Im F(x + iy), with
+//                        Dawson's F from its complex Taylor series around the nearest
+//                        node x_c (step 0.25). This form keeps relative accuracy in the
+//                        Gaussian tail near the real axis, where Re w is tiny next to Im w.
+// The continued fraction truncations miss the exponentially small e^{-z^2} part of w,
+// which matters only near the real axis at |x| < 6; it is added back there.
+#pragma once
+#include <math.h>
+
+#ifdef __CUDACC__
+#define ROX_FN __device__ __forceinline__
+#define ROX_TABLE static __constant__ const
+#else
+#define ROX_FN static inline
+#define ROX_TABLE static const
+#endif
+
+#include "rox_faddeeva_tables.h"
+
+#define ROX_INV_SQRT_PI 0.564189583547756287f
+#define ROX_TWO_INV_SQRT_PI 1.128379167095512574f
+
+// region boundaries on s = x^2 + y^2
+#define ROX_S_FAR 484.0f     // 22^2
+#define ROX_S_CF3 100.0f     // 10^2
+#define ROX_S_CF5 36.0f      // 6^2
+#define ROX_S_CF8 20.25f     // 4.5^2
+#define ROX_Y_WEIDEMAN 0.1f
+
+ROX_FN float rox_rcp(float v) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+#else
+  return 1.0f / v;
+#endif
+}
+
+// e^{y^2 - x^2} cos(2xy): the part of w(z) = e^{-z^2} + (2i/sqrt(pi)) F(z) that the
+// asymptotic (continued fraction) forms do not contain.
+ROX_FN float rox_gauss_part(float x, float y) {
+  return expf((y - x) * (y + x)) * cosf(2.0f * x * y);
+}
+
+// 2-level continued fraction: w ~ (i/sqrt(pi)) z / (z^2 - 1/2).
+// Re = y (s + 1/2) / (sqrt(pi) ((s - 1/2)^2 + 2 y^2)).
+ROX_FN float rox_re_w_cf2(float x, float y) {
+  float v = y * y;
+  float s = fmaf(x, x, v);
+  float t = s - 0.5f;
+  float d = fmaf(t, t, 2.0f * v);
+  return ROX_INV_SQRT_PI * y * (s + 0.5f) * rox_rcp(d);
+}
+
+// complex multiply-add helpers on (re, im) pairs
+struct rox_c { float r, i; };
+ROX_FN rox_c rox_cmul(rox_c a, rox_c b) {
+  rox_c o;
+  o.r = fmaf(a.r, b.r, -a.i * b.i);
+  o.i = fmaf(a.r, b.i, a.i * b.r);
+  return o;
+}
+
+// Horner in zeta = z^2 with real coefficients c[0..n-1] (highest first)
+template <int N>
+ROX_FN rox_c rox_horner_zeta(const float* c, rox_c zeta) {
+  rox_c acc;
+  acc.r = c[0];
+  acc.i = 0.0f;
+#pragma unroll
+  for (int k = 1; k < N; k++) {
+    rox_c m = rox_cmul(acc, zeta);
+    acc.r = m.r + c[k];
+    acc.i = m.i;
+  }
+  return acc;
+}
+
+// n-level continued fraction truncation w ~ (i/sqrt(pi)) A(z)/B(z), with
+// A = z^{a_odd} a(z^2), B = z^{1-a_odd} b(z^2). Re w = -Im(A conj(B)) / (sqrt(pi) |B|^2).
+template <int NA, int NB, int AODD>
+ROX_FN float rox_re_w_cf(const float* ca, const float* cb, float x, float y) {
+  rox_c zeta;
+  zeta.r = (x - y) * (x + y);
+  zeta.i = 2.0f * x * y;
+  rox_c a = rox_horner_zeta<NA>(ca, zeta);
+  rox_c b = rox_horner_zeta<NB>(cb, zeta);
+  rox_c z;
+  z.r = x;
+  z.i = y;
+  if (AODD) a = rox_cmul(a, z); else b = rox_cmul(b, z);
+  float num = fmaf(a.r, b.i, -a.i * b.r);          // -Im(A conj B) = A_r B_i - A_i B_r
+  float den = fmaf(b.r, b.r, b.i * b.i);
+  return ROX_INV_SQRT_PI * num * rox_rcp(den);
+}
+
+// 3-level: A = z^2 - 1, B = z (z^2 - 3/2)
+ROX_FN float rox_re_w_cf3(float x, float y) {
+  const float ca[2] = {1.0f, -1.0f};
+  const float cb[2] = {1.0f, -1.5f};
+  return rox_re_w_cf<2, 2, 0>(ca, cb, x, y);
+}
+
+ROX_FN float rox_re_w_cf5(float x, float y) {
+  return rox_re_w_cf<3, 3, ROX_CF5_A_ODD>(rox_cf5_a, rox_cf5_b, x, y);
+}
+
+ROX_FN float rox_re_w_cf8(float x, float y) {
+  return rox_re_w_cf<4, 5, ROX_CF8_A_ODD>(rox_cf8_a, rox_cf8_b, x, y);
+}
+
+// Weideman (1994): w(z) ~ [2 p(Z) + (L - iz)/sqrt(pi)] / (L - iz)^2, Z = (L + iz)/(L - iz).
+ROX_FN float rox_re_w_weideman(float x, float y) {
+  const float L = ROX_WEI_L;
+  float lpy = L + y;
+  float q2 = rox_rcp(fmaf(lpy, lpy, x * x));        // 1/|L - iz|^2
+  rox_c q;                                           // 1/(L - iz) = (L + y + ix)/|L - iz|^2
+  q.r = lpy * q2;
+  q.i = x * q2;
+  rox_c Z;                                           // ((L^2 - s) + 2iLx)/|L - iz|^2
+  Z.r = (fmaf(L, L, -fmaf(x, x, y * y))) * q2;
+  Z.i = 2.0f * L * x * q2;
+  rox_c p;
+  p.r = rox_wei_a[0];
+  p.i = 0.0f;
+#pragma unroll
+  for (int k = 1; k < ROX_WEI_N; k++) {
+    rox_c m = rox_cmul(p, Z);
+    p.r = m.r + rox_wei_a[k];
+    p.i = m.i;
+  }
+  rox_c t = rox_cmul(p, q);                          // p/(L - iz)
+  t.r = fmaf(2.0f, t.r, ROX_INV_SQRT_PI);
+  t.i = 2.0f * t.i;
+  return fmaf(t.r, q.r, -t.i * q.i);                 // Re[(2p/(L-iz) + 1/sqrt(pi)) / (L-iz)]
+}
+
+// Near the real axis: Re w = e^{y^2-x^2} cos 2xy - (2/sqrt(pi)) Im F(x+iy), F Dawson's
+// integral from its Taylor series at the nearest node, evaluated at the complex offset
+// (x - x_c) + iy by complex Horner (imaginary parts stay O(y), so the O(y) result keeps
+// its relative accuracy). `tab` is rox_daw_taylor, possibly copied to shared memory.
+ROX_FN float rox_re_w_dawson(const float* tab, float x, float y) {
+  int node = (int)rintf(x * ROX_DAW_INV_STEP);
+  node = node > ROX_DAW_NODES - 1 ? ROX_DAW_NODES - 1 : (node < 0 ? 0 : node);
+  const float* d = tab + node * (ROX_DAW_DEG + 1);
+  float t = fmaf(-(float)node, ROX_DAW_STEP, x);
+  float ar = d[ROX_DAW_DEG], ai = 0.0f;
+#pragma unroll
+  for (int n = ROX_DAW_DEG - 1; n >= 0; n--) {
+    float nr = fmaf(ar, t, fmaf(-ai, y, d[n]));
+    float ni = fmaf(ar, y, ai * t);
+    ar = nr;
+    ai = ni;
+  }
+  return fmaf(-ROX_TWO_INV_SQRT_PI, ai, rox_gauss_part(x, y));
+}
+
+// Re w(x + iy) for x any sign, y >= 0, all regions. `daw` points at rox_daw_taylor.
+ROX_FN float rox_re_w(const float* daw, float x, float y) {
+  x = fabsf(x);
+  float s = fmaf(x, x, y * y);
+  if (s >= ROX_S_FAR) return rox_re_w_cf2(x, y);
+  if (s >= ROX_S_CF3) return rox_re_w_cf3(x, y);
+  if (s >= ROX_S_CF5) {
+    float r = rox_re_w_cf5(x, y);
+    return y < 1e-6f ? r + rox_gauss_part(x, y) : r;
+  }
+  if (s >= ROX_S_CF8) {
+    float r = rox_re_w_cf8(x, y);
+    return y < 1.0f ? r + rox_gauss_part(x, y) : r;
+  }
+  if (y >= ROX_Y_WEIDEMAN) return rox_re_w_weideman(x, y);
+  return rox_re_w_dawson(daw, x, y);
+}

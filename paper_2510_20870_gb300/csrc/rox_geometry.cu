@@ -1,0 +1,192 @@
+// a3: sort by nu0, per-line grid windows and centre decomposition, per-tile line ranges.
+// pyROX paper, "Combine and save": the line profiles are summed into a cross-section on
+// the user's grid for each temperature-pressure point. With the lines sorted by nu0 and
+// a hard wing cutoff, the lines that reach a wavenumber tile form one contiguous range,
+// found here without atomics from the sorted order.
+#include <cub/device/device_radix_sort.cuh>
+#include <cuda_fp16.h>
+#include "rox_internal.cuh"
+
+namespace {
+
+// d_j = (nu_min + j*dnu) - nu0 with each operation rounded separately (no contraction),
+// exactly the double-precision expression of the cutoff test.
+__device__ __forceinline__ double node_offset(double nu_min, double dnu, long long j, double nu0) {
+  return __dsub_rn(__dadd_rn(nu_min, __dmul_rn((double)j, dnu)), nu0);
+}
+
+__global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, double nu_min,
+                          double dnu, long long n_grid, double cutoff, int32_t* jlo_out,
+                          int32_t* jhi_out, int32_t* k0_out, float* f_out, float4* geo_out,
+                          unsigned long long* evals_out, int32_t* unsorted_out, int32_t unsorted_value) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long ev = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_lines; i += stride) {
+    double nu0 = nu0s[i];
+    if (i > 0 && nu0s[i - 1] > nu0 && unsorted_out) *unsorted_out = unsorted_value;
+    // first j with d_j >= -cutoff, last j with d_j <= cutoff (d_j non-decreasing in j)
+    double lo_c = ceil((nu0 - cutoff - nu_min) / dnu);
+    double hi_c = floor((nu0 + cutoff - nu_min) / dnu);
+    lo_c = fmin(fmax(lo_c, -4.0), (double)n_grid + 4.0);
+    hi_c = fmin(fmax(hi_c, -4.0), (double)n_grid + 4.0);
+    long long jlo = (long long)lo_c, jhi = (long long)hi_c;
+    for (int it = 0; it < 4 && node_offset(nu_min, dnu, jlo - 1, nu0) >= -cutoff; it++) jlo--;
+    for (int it = 0; it < 4 && node_offset(nu_min, dnu, jlo, nu0) < -cutoff; it++) jlo++;
+    for (int it = 0; it < 4 && node_offset(nu_min, dnu, jhi + 1, nu0) <= cutoff; it++) jhi++;
+    for (int it = 0; it < 4 && node_offset(nu_min, dnu, jhi, nu0) > cutoff; it++) jhi--;
+    long long jl = jlo < 0 ? 0 : (jlo > n_grid ? n_grid : jlo);
+    long long jh = jhi < -1 ? -1 : (jhi > n_grid - 1 ? n_grid - 1 : jhi);
+    if (jh >= jl) ev += (unsigned long long)(jh - jl + 1);
+    // centre decomposition (nu0 - nu_min)/dnu = k0 + f
+    double u = (nu0 - nu_min) / dnu;
+    double k0 = floor(u);
+    double f = u - k0;
+    if (f >= 1.0) { k0 += 1.0; f -= 1.0; }
+    if (jh < jl) { k0 = 0.0; f = 0.0; }       // touches no grid point: never evaluated
+    if (jlo_out) jlo_out[i] = (int32_t)jl;
+    if (jhi_out) jhi_out[i] = (int32_t)jh;
+    if (k0_out) k0_out[i] = (int32_t)k0;
+    if (f_out) f_out[i] = (float)f;
+    if (geo_out)
+      geo_out[i] = make_float4((float)k0, (float)(f * dnu), __int_as_float((int)jl), __int_as_float((int)jh));
+  }
+  if (evals_out) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evals_out, ev);
+  }
+}
+
+// Tile t meets line i iff jhi_i >= t*W and jlo_i <= (t+1)*W - 1. Both bounds are
+// non-decreasing along the sorted list, so lo[t] = first i with jhi_i >= t*W and
+// hi[t] = first i with jlo_i >= (t+1)*W. Each line writes the boundaries between its
+// predecessor's tile count and its own (the sorted-order form of a histogram prefix sum).
+__device__ __forceinline__ long long tiles_reached_hi(int32_t jhi, int32_t W, long long n_tiles) {
+  if (jhi < 0) return 0;
+  long long c = (long long)jhi / W + 1;
+  return c < n_tiles ? c : n_tiles;
+}
+__device__ __forceinline__ long long tiles_passed_lo(int32_t jlo, int32_t W, long long n_tiles) {
+  long long c = (long long)jlo / W;
+  return c < n_tiles ? c : n_tiles;
+}
+
+__global__ void k_tile_ranges(const int32_t* __restrict__ jlo, const int32_t* __restrict__ jhi,
+                              long long n_lines, long long n_tiles, int32_t W,
+                              long long* lo_out, long long* hi_out) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= n_lines; i += stride) {
+    long long ch_prev = i > 0 ? tiles_reached_hi(jhi[i - 1], W, n_tiles) : 0;
+    long long cl_prev = i > 0 ? tiles_passed_lo(jlo[i - 1], W, n_tiles) : 0;
+    long long ch = i < n_lines ? tiles_reached_hi(jhi[i], W, n_tiles) : n_tiles;
+    long long cl = i < n_lines ? tiles_passed_lo(jlo[i], W, n_tiles) : n_tiles;
+    for (long long t = ch_prev; t < ch; t++) lo_out[t] = i;
+    for (long long t = cl_prev; t < cl; t++) hi_out[t] = i;
+  }
+}
+
+// same, reading the window bounds out of the packed geometry records
+__global__ void k_tile_ranges_geo(const float4* __restrict__ geo, long long n_lines, long long n_tiles,
+                                  int32_t W, long long* lo_out, long long* hi_out) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= n_lines; i += stride) {
+    long long ch_prev = 0, cl_prev = 0, ch = n_tiles, cl = n_tiles;
+    if (i > 0) {
+      float4 g = geo[i - 1];
+      ch_prev = tiles_reached_hi(__float_as_int(g.w), W, n_tiles);
+      cl_prev = tiles_passed_lo(__float_as_int(g.z), W, n_tiles);
+    }
+    if (i < n_lines) {
+      float4 g = geo[i];
+      ch = tiles_reached_hi(__float_as_int(g.w), W, n_tiles);
+      cl = tiles_passed_lo(__float_as_int(g.z), W, n_tiles);
+    }
+    for (long long t = ch_prev; t < ch; t++) lo_out[t] = i;
+    for (long long t = cl_prev; t < cl; t++) hi_out[t] = i;
+  }
+}
+
+__global__ void k_iota(int32_t* v, long long n) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v[i] = (int32_t)i;
+}
+
+template <typename T>
+__global__ void k_gather(const T* __restrict__ src, const int32_t* __restrict__ perm, T* dst, long long n) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[perm[i]];
+}
+
+__global__ void k_perm64(const int32_t* __restrict__ perm, long long* out, long long n) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = perm[i];
+}
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+size_t cub_temp_bytes(long long n) {
+  size_t tb = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, tb, (const unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                  (const int32_t*)nullptr, (int32_t*)nullptr, (int64_t)n, 0, 63);
+  return tb;
+}
+
+}  // namespace
+
+cudaError_t rox_launch_windows(const double* nu0, long long n_lines, const rox_grid* g, double cutoff,
+                               int32_t* jlo, int32_t* jhi, int32_t* k0, float* f, float4* geo,
+                               unsigned long long* evals, int32_t* unsorted, int32_t unsorted_value,
+                               cudaStream_t s) {
+  k_windows<<<grid_for(n_lines), 256, 0, s>>>(nu0, n_lines, g->nu_min, g->dnu, g->n, cutoff, jlo, jhi, k0,
+                                               f, geo, evals, unsorted, unsorted_value);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_tile_ranges(const int32_t* jlo, const int32_t* jhi, long long n_lines, long long n_tiles,
+                                   int32_t W, long long* lo, long long* hi, cudaStream_t s) {
+  k_tile_ranges<<<grid_for(n_lines + 1), 256, 0, s>>>(jlo, jhi, n_lines, n_tiles, W, lo, hi);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_tile_ranges_geo(const float4* geo, long long n_lines, long long n_tiles, int32_t W,
+                                       long long* lo, long long* hi, cudaStream_t s) {
+  k_tile_ranges_geo<<<grid_for(n_lines + 1), 256, 0, s>>>(geo, n_lines, n_tiles, W, lo, hi);
+  return cudaGetLastError();
+}
+
+size_t rox_sort_ws_bytes(long long n) {
+  return rox_align256(cub_temp_bytes(n)) + rox_align256((size_t)n * 8) + 2 * rox_align256((size_t)n * 4) + 256;
+}
+
+cudaError_t rox_launch_sort(const rox_lines* in, const rox_lines_buf* out, int64_t* perm_out, void* ws,
+                            cudaStream_t s) {
+  long long n = in->n;
+  char* p = (char*)ws;
+  size_t tb = cub_temp_bytes(n);
+  void* temp = p; p += rox_align256(tb);
+  unsigned long long* keys_out = (unsigned long long*)p; p += rox_align256((size_t)n * 8);
+  int32_t* idx_in = (int32_t*)p; p += rox_align256((size_t)n * 4);
+  int32_t* idx_out = (int32_t*)p;
+  k_iota<<<grid_for(n), 256, 0, s>>>(idx_in, n);
+  // positive doubles order like their bit patterns; bit 63 (sign) is zero for nu0 > 0
+  cudaError_t e = cub::DeviceRadixSort::SortPairs(temp, tb, (const unsigned long long*)in->nu0, keys_out,
+                                                  idx_in, idx_out, (int64_t)n, 0, 63, s);
+  if (e != cudaSuccess) return e;
+  int gb = grid_for(n);
+  k_gather<double><<<gb, 256, 0, s>>>(in->nu0, idx_out, out->nu0, n);
+  k_gather<float><<<gb, 256, 0, s>>>(in->s_or_a, idx_out, out->s_or_a, n);
+  if (in->convention == ROX_EXOMOL) k_gather<float><<<gb, 256, 0, s>>>(in->g_up, idx_out, out->g_up, n);
+  k_gather<float><<<gb, 256, 0, s>>>(in->e_lower, idx_out, out->e_lower, n);
+  if (in->width_dtype == ROX_WIDTH_F16) {
+    k_gather<__half><<<gb, 256, 0, s>>>((const __half*)in->gamma_ref, idx_out, (__half*)out->gamma_ref, n);
+    k_gather<__half><<<gb, 256, 0, s>>>((const __half*)in->n_t, idx_out, (__half*)out->n_t, n);
+  } else {
+    k_gather<float><<<gb, 256, 0, s>>>((const float*)in->gamma_ref, idx_out, (float*)out->gamma_ref, n);
+    k_gather<float><<<gb, 256, 0, s>>>((const float*)in->n_t, idx_out, (float*)out->n_t, n);
+  }
+  if (perm_out) k_perm64<<<gb, 256, 0, s>>>(idx_out, (long long*)perm_out, n);
+  return cudaGetLastError();
+}

@@ -1,0 +1,127 @@
+// a1 / a2: per-line strength S(T) and widths gamma_G, gamma_L.
+// pyROX paper, "Functionality of pyROX" -- "Compute line-strengths and -widths": the
+// strength and broadening widths of every transition at the user's pressure and
+// temperature. HBM-bound kernels: each thread reads one line's SoA entries (coalesced)
+// and writes its outputs; the Boltzmann and stimulated-emission factors and the partition
+// ratio are taken in FP64.
+#include <cuda_fp16.h>
+#include "rox_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ float load_width(const void* p, int f16, long long i) {
+  return f16 ? __half2float(reinterpret_cast<const __half*>(p)[i])
+             : reinterpret_cast<const float*>(p)[i];
+}
+
+struct StrengthConsts {
+  int convention;
+  double inv_T;        // 1/T
+  double q_ratio;      // HITRAN: Q_ref/Q_T ; ExoMol: 1/Q_T
+  double c2_dT;        // HITRAN: c2 (1/T - 1/T_ref) ; ExoMol: c2/T
+};
+
+// S(T) in FP64 for one line (HITRAN S_ref form or ExoMol Einstein-A form).
+__device__ __forceinline__ double line_strength(const StrengthConsts& k, double nu0, double s_or_a,
+                                                double g_up, double e_lower) {
+  double stim_T = -expm1(-ROX_C2 * nu0 * k.inv_T);           // 1 - exp(-c2 nu0 / T)
+  double boltz = exp(-e_lower * k.c2_dT);
+  if (k.convention == ROX_HITRAN) {
+    double stim_ref = -expm1(-ROX_C2 * nu0 / ROX_T_REF);
+    return s_or_a * k.q_ratio * boltz * (stim_T / stim_ref);
+  }
+  return g_up * s_or_a / (8.0 * ROX_PI * ROX_C_CM * nu0 * nu0) * boltz * stim_T * k.q_ratio;
+}
+
+__global__ void k_strengths(rox_lines L, StrengthConsts k, float* S_out) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) {
+    double g = (L.convention == ROX_EXOMOL) ? (double)L.g_up[i] : 1.0;
+    S_out[i] = (float)line_strength(k, L.nu0[i], (double)L.s_or_a[i], g, (double)L.e_lower[i]);
+  }
+}
+
+__global__ void k_widths(rox_lines L, double gG_fac, float l2_ratio, float p_fac,
+                         float* gG_out, float* gL_out) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  int f16 = L.width_dtype == ROX_WIDTH_F16;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) {
+    gG_out[i] = (float)(L.nu0[i] * gG_fac);
+    float gref = load_width(L.gamma_ref, f16, i);
+    float nt = load_width(L.n_t, f16, i);
+    gL_out[i] = gref * exp2f(nt * l2_ratio) * p_fac;
+  }
+}
+
+// S(T) for up to ROX_MAX_PT distinct temperatures in one launch, one sweep over the lines
+// per temperature (the FP64 exponentials, not the bytes, set its cost); the per-temperature maximum (needed to
+// scale S into FP32 range inside the Voigt kernel) is reduced per warp and combined with
+// an atomic max on the (non-negative) double bit pattern, which is order-independent.
+struct TempSet {
+  int n;
+  StrengthConsts k[ROX_MAX_PT];
+};
+
+__global__ void k_strengths_multi(rox_lines L, TempSet ts,
+                                  double* S_T, unsigned long long* smax_bits) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (int t = 0; t < ts.n; t++) {
+    double mx = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) {
+      double g = (L.convention == ROX_EXOMOL) ? (double)L.g_up[i] : 1.0;
+      double s = line_strength(ts.k[t], L.nu0[i], (double)L.s_or_a[i], g, (double)L.e_lower[i]);
+      S_T[(long long)t * L.n + i] = s;
+      mx = fmax(mx, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.0)
+      atomicMax(&smax_bits[t], (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+StrengthConsts make_consts(int convention, double T, double Q_T, double Q_ref) {
+  StrengthConsts k;
+  k.convention = convention;
+  k.inv_T = 1.0 / T;
+  if (convention == ROX_HITRAN) {
+    k.q_ratio = Q_ref / Q_T;
+    k.c2_dT = ROX_C2 * (1.0 / T - 1.0 / ROX_T_REF);
+  } else {
+    k.q_ratio = 1.0 / Q_T;
+    k.c2_dT = ROX_C2 / T;
+  }
+  return k;
+}
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+}  // namespace
+
+cudaError_t rox_launch_strengths(const rox_lines* L, double T, double Q_T, double Q_ref,
+                                 float* S_out, cudaStream_t s) {
+  k_strengths<<<grid_for(L->n), 256, 0, s>>>(*L, make_consts(L->convention, T, Q_T, Q_ref), S_out);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_widths(const rox_lines* L, double mass_amu, double P_bar, double T,
+                              float* gG, float* gL, cudaStream_t s) {
+  double gG_fac = sqrt(2.0 * ROX_KB * T / (mass_amu * ROX_AMU)) / ROX_C_M;
+  float l2 = (float)log2(ROX_T_REF / T);
+  float pf = (float)(P_bar / ROX_P_REF);
+  k_widths<<<grid_for(L->n), 256, 0, s>>>(*L, gG_fac, l2, pf, gG, gL);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_strengths_multi(const rox_lines* L, int n_temps, const double* temps,
+                                       const double* q_of_temp, double Q_ref, double* S_T,
+                                       unsigned long long* smax_bits, cudaStream_t s) {
+  TempSet ts;
+  ts.n = n_temps;
+  for (int t = 0; t < n_temps; t++) ts.k[t] = make_consts(L->convention, temps[t], q_of_temp[t], Q_ref);
+  k_strengths_multi<<<grid_for(L->n), 256, 0, s>>>(*L, ts, S_T, smax_bits);
+  return cudaGetLastError();
+}
