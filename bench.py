@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--lines", type=int, default=None,
+                    help="use only the first N lines of the workload (smaller profiling case)")
     return ap.parse_args()
 
 
@@ -225,7 +228,7 @@ def run_gpu(args):
 
     w, grid, P, T, q = workload(args.config)
     Qt, Qr = q_of(q, T), q_of(q, 296.0)
-    host = rs.make_lines(w)                   # unsorted, generation order
+    host = rs.make_lines(w, 0, args.lines)     # unsorted, generation order
     cols = ["nu0", "s_or_a", "g_up", "e_lower", "gamma_ref", "n_t"]
     pinned = {k: torch.from_numpy(host[k]).pin_memory() for k in cols if host[k] is not None}
     raw = {k: torch.empty_like(v, device=dev) for k, v in pinned.items()}
@@ -290,14 +293,15 @@ def run_gpu(args):
     value = world * evals * args.steps / (ms * 1e-3)
 
     # ---- end to end through the public API: pinned host -> device, sort, xsec, sigma -> host
-    for _ in range(max(1, args.warmup // 2)):
+    e2e_steps = 0 if args.no_e2e else args.steps
+    for _ in range(max(1, args.warmup // 2) if e2e_steps else 0):
         upload_and_sort()
         step()
         sigma_host.copy_(sigma, non_blocking=True)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         upload_and_sort()
         step()
         sigma_host.copy_(sigma, non_blocking=True)
@@ -308,7 +312,7 @@ def run_gpu(args):
         tt = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
-    e2e_value = world * evals * args.steps / (e2e_ms * 1e-3)
+    e2e_value = world * evals * e2e_steps / (e2e_ms * 1e-3) if e2e_steps else None
     assert np.isfinite(sigma_host.numpy()).all()
 
     csum = clocks.summary()
@@ -334,7 +338,7 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "%s: %d lines (ExoMol-style), grid %g-%g cm^-1 at %g (%d points), cutoff %g "
-                           "cm^-1, (P,T)=(%g bar, %g K)" % (w.name, w.n_lines, w.grid_lo, w.grid_hi, w.dnu, grid[2],
+                           "cm^-1, (P,T)=(%g bar, %g K)" % (w.name, n, w.grid_lo, w.grid_hi, w.dnu, grid[2],
                                                            w.cutoff, P, T),
                            "evals_per_step": evals, "xsecs_per_s": world * args.steps / (ms * 1e-3),
                            "step": "rox_xsec on the resident nu0-sorted list (strengths, widths, windows, tile "
@@ -344,7 +348,8 @@ def run_gpu(args):
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
-                        "d2h_bytes_per_step": sigma.numel() * 4, "ms_per_step": e2e_ms / args.steps,
+                        "d2h_bytes_per_step": sigma.numel() * 4,
+                        "ms_per_step": e2e_ms / e2e_steps if e2e_steps else None,
                         "includes": "H2D of the unsorted list, rox_sort_lines, rox_xsec, D2H of sigma"},
                 "gpu_launches": args.steps * 4,
                 "gpu_launches_note": "per step: windows, strengths, tile ranges, Voigt kernels (+1 memset)",

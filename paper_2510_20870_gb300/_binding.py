@@ -18,7 +18,7 @@ ROX_HITRAN, ROX_EXOMOL = 0, 1
 ROX_WIDTH_F32, ROX_WIDTH_F16 = 0, 1
 ROX_ACCUMULATE = 1
 ROX_MAX_PT = 512
-ROX_TILE = 2048  # grid points per CTA tile (ROX_THREADS * ROX_K)
+ROX_TILE = 256  # grid points per Voigt work item (one warp: 32 lanes x ROX_K points)
 
 
 class RoxError(RuntimeError):

@@ -5,7 +5,7 @@ Run: python gen_faddeeva_tables.py > rox_faddeeva_tables.h  (build() checks it i
 Everything is derived here from mathematics, with exact rational arithmetic where
 it matters; no special-function library is called:
   * Taylor coefficients of Dawson's integral F(x) = exp(-x^2) int_0^x exp(t^2) dt
-    around nodes x_c = 0, 0.25, ..., 4.5, from its Maclaurin series
+    around nodes x_c = 0, 0.25, ..., 6.0, from its Maclaurin series
     F(x) = sum_k (-1)^k 2^k x^(2k+1) / (2k+1)!!  (exact rationals, summed to 1e-60)
     and the ODE F' = 1 - 2 x F, which gives (n+1) d_{n+1} = [n=0] - 2 x_c d_n - 2 d_{n-1}.
   * Weideman's rational approximation (J.A.C. Weideman, SIAM J. Numer. Anal. 31 (1994)
@@ -20,7 +20,7 @@ from fractions import Fraction as Fr
 import numpy as np
 
 DAW_STEP = Fr(1, 4)      # node spacing
-DAW_NODES = 19           # x_c = 0 .. 4.5
+DAW_NODES = 25           # x_c = 0 .. 6.0
 DAW_DEG = 12
 WEI_N = 20
 
@@ -106,7 +106,7 @@ def main():
     out.append("#define ROX_WEI_L %s" % f32(L))
     out.append("/* a_N .. a_1 (Horner order) */")
     out.append("ROX_TABLE float rox_wei_a[ROX_WEI_N] = {" + ", ".join(f32(v) for v in a) + "};")
-    for n in (5, 8):
+    for n in (5,):
         A, B = cf_polys(n)
         ca, pa = even_part_in_zeta(A)
         cb, pb = even_part_in_zeta(B)

@@ -17,6 +17,8 @@ cudaError_t rox_launch_widths(const rox_lines* L, double mass_amu, double P_bar,
 cudaError_t rox_launch_strengths_multi(const rox_lines* L, int n_temps, const double* temps,
                                        const double* q_of_temp, double Q_ref, double* S_T,
                                        unsigned long long* smax_bits, cudaStream_t s);
+cudaError_t rox_launch_scale_strengths(const double* S_T, long long n, int n_temps,
+                                       const unsigned long long* smax_bits, float* S32, cudaStream_t s);
 cudaError_t rox_launch_windows(const double* nu0, long long n_lines, const rox_grid* g, double cutoff,
                                int32_t* jlo, int32_t* jhi, int32_t* k0, float* f, float4* geo,
                                unsigned long long* evals, int32_t* unsorted, int32_t unsorted_value,
@@ -101,6 +103,7 @@ struct WsLayout {
   long long* tlo;
   long long* thi;
   double* S_T;
+  float* S32;
   size_t bytes;
 };
 
@@ -119,6 +122,8 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps) {
   off += rox_align256((size_t)nt * 8);
   w.S_T = (double*)(base + off);
   off += rox_align256((size_t)n_temps * (size_t)(n_lines > 0 ? n_lines : 1) * 8);
+  w.S32 = (float*)(base + off);
+  off += rox_align256((size_t)n_temps * (size_t)(n_lines > 0 ? n_lines : 1) * 4);
   w.bytes = off;
   return w;
 }
@@ -269,7 +274,7 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
 
   static thread_local RoxVoigtArgs A;   // 8 KB of per-point parameters, passed by value
   A.geo = w.geo;
-  A.S_T = w.S_T;
+  A.S32 = w.S32;
   A.gamma_ref = lines->gamma_ref;
   A.n_t = lines->n_t;
   A.width_f16 = lines->width_dtype == ROX_WIDTH_F16;
@@ -301,6 +306,9 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
     if ((rc = cuda_check(rox_launch_strengths_multi(lines, n_temps, temps.data(), qs.data(), Q_ref, w.S_T,
                                                     w.hdr->smax_bits, s),
                          "strengths kernel")))
+      return rc;
+    if ((rc = cuda_check(rox_launch_scale_strengths(w.S_T, nl, n_temps, w.hdr->smax_bits, w.S32, s),
+                         "strength scaling kernel")))
       return rc;
   }
   if ((rc = cuda_check(rox_launch_tile_ranges_geo(w.geo, nl, nt, ROX_TILE, w.tlo, w.thi, s), "tile ranges")))

@@ -6,18 +6,17 @@
 //
 // Region split on s = x^2 + y^2 (x >= 0; Re w is even in x), each method written
 // from its published definition and checked against wofz (max relative error of
-// Re w about 1e-5 over x in [0, 1e5], y in [0, 1e4]):
+// Re w about 1.1e-5 over x in [0, 1e5], y in [0, 1e4]):
 //   s >= 22^2          2-level Laplace continued fraction (Humlicek 1982, region I form)
-//   10^2 <= s < 22^2   3-level continued fraction
+//   10^2 <= s < 22^2   3-level continued fraction, in closed real form
 //   6^2  <= s < 10^2   5-level continued fraction (+ Gaussian term for y < 1e-6)
-//   4.5^2 <= s < 6^2   8-level continued fraction + e^{y^2-x^2} cos(2xy) for y < 1
-//   s < 4.5^2, y >= 0.1  Weideman (1994) rational approximation, N = 20
-//   s < 4.5^2, y <  0.1  Re w = e^{y^2-x^2} cos(2xy) - (2/sqrt(pi)) Im F(x + iy), with
-//                        Dawson's F from its complex Taylor series around the nearest
-//                        node x_c (step 0.25). This form keeps relative accuracy in the
-//                        Gaussian tail near the real axis, where Re w is tiny next to Im w.
+//   s < 6^2, y >= 0.1  Weideman (1994) rational approximation, N = 20
+//   s < 6^2, y <  0.1  Re w = e^{y^2-x^2} cos(2xy) - (2/sqrt(pi)) Im F(x + iy), with
+//                      Dawson's F from its complex Taylor series around the nearest
+//                      node x_c (step 0.25). This form keeps relative accuracy in the
+//                      Gaussian tail near the real axis, where Re w is tiny next to Im w.
 // The continued fraction truncations miss the exponentially small e^{-z^2} part of w,
-// which matters only near the real axis at |x| < 6; it is added back there.
+// which can matter just outside |z| = 6 when y is essentially zero; it is added there.
 #pragma once
 #include <math.h>
 
@@ -38,7 +37,6 @@
 #define ROX_S_FAR 484.0f     // 22^2
 #define ROX_S_CF3 100.0f     // 10^2
 #define ROX_S_CF5 36.0f      // 6^2
-#define ROX_S_CF8 20.25f     // 4.5^2
 #define ROX_Y_WEIDEMAN 0.1f
 
 ROX_FN float rox_rcp(float v) {
@@ -109,19 +107,20 @@ ROX_FN float rox_re_w_cf(const float* ca, const float* cb, float x, float y) {
   return ROX_INV_SQRT_PI * num * rox_rcp(den);
 }
 
-// 3-level: A = z^2 - 1, B = z (z^2 - 3/2)
+// 3-level: w ~ (i/sqrt(pi)) (z^2 - 1) / (z^3 - 3z/2). With u = x^2, v = y^2, s = u + v:
+// Re w = y (s^2 - 3s/2 + 4v + 3/2) / (sqrt(pi) [u (u - 3v - 3/2)^2 + v (3u - v - 3/2)^2]).
 ROX_FN float rox_re_w_cf3(float x, float y) {
-  const float ca[2] = {1.0f, -1.0f};
-  const float cb[2] = {1.0f, -1.5f};
-  return rox_re_w_cf<2, 2, 0>(ca, cb, x, y);
+  const float u = x * x, v = y * y;
+  const float s = u + v;
+  const float num = fmaf(s, s - 1.5f, fmaf(4.0f, v, 1.5f));
+  const float a = u - fmaf(3.0f, v, 1.5f);
+  const float b = fmaf(3.0f, u, -(v + 1.5f));
+  const float den = fmaf(u * a, a, (v * b) * b);
+  return ROX_INV_SQRT_PI * y * num * rox_rcp(den);
 }
 
 ROX_FN float rox_re_w_cf5(float x, float y) {
   return rox_re_w_cf<3, 3, ROX_CF5_A_ODD>(rox_cf5_a, rox_cf5_b, x, y);
-}
-
-ROX_FN float rox_re_w_cf8(float x, float y) {
-  return rox_re_w_cf<4, 5, ROX_CF8_A_ODD>(rox_cf8_a, rox_cf8_b, x, y);
 }
 
 // Weideman (1994): w(z) ~ [2 p(Z) + (L - iz)/sqrt(pi)] / (L - iz)^2, Z = (L + iz)/(L - iz).
@@ -170,20 +169,23 @@ ROX_FN float rox_re_w_dawson(const float* tab, float x, float y) {
   return fmaf(-ROX_TWO_INV_SQRT_PI, ai, rox_gauss_part(x, y));
 }
 
+// 5-level fraction with the Gaussian part kept for (essentially) zero y
+ROX_FN float rox_re_w_cf5g(float x, float y) {
+  float r = rox_re_w_cf5(x, y);
+  return y < 1e-6f ? r + rox_gauss_part(x, y) : r;
+}
+
+// |z| < 6: Weideman away from the real axis, the Dawson form near it (y is per line)
+ROX_FN float rox_re_w_core(const float* daw, float x, float y) {
+  return y >= ROX_Y_WEIDEMAN ? rox_re_w_weideman(x, y) : rox_re_w_dawson(daw, x, y);
+}
+
 // Re w(x + iy) for x any sign, y >= 0, all regions. `daw` points at rox_daw_taylor.
 ROX_FN float rox_re_w(const float* daw, float x, float y) {
   x = fabsf(x);
   float s = fmaf(x, x, y * y);
   if (s >= ROX_S_FAR) return rox_re_w_cf2(x, y);
   if (s >= ROX_S_CF3) return rox_re_w_cf3(x, y);
-  if (s >= ROX_S_CF5) {
-    float r = rox_re_w_cf5(x, y);
-    return y < 1e-6f ? r + rox_gauss_part(x, y) : r;
-  }
-  if (s >= ROX_S_CF8) {
-    float r = rox_re_w_cf8(x, y);
-    return y < 1.0f ? r + rox_gauss_part(x, y) : r;
-  }
-  if (y >= ROX_Y_WEIDEMAN) return rox_re_w_weideman(x, y);
-  return rox_re_w_dawson(daw, x, y);
+  if (s >= ROX_S_CF5) return rox_re_w_cf5g(x, y);
+  return rox_re_w_core(daw, x, y);
 }

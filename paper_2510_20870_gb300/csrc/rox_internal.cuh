@@ -15,13 +15,14 @@
 #define ROX_P_REF 1.01325               // bar, 1 atm
 #define ROX_PI 3.14159265358979323846
 
-// Voigt tile geometry: 8 warps per CTA, each thread owns ROX_K grid points strided by 32,
-// so one warp covers 32*ROX_K consecutive points and a CTA tile ROX_TILE points.
+// Voigt work geometry: a warp owns one span of ROX_SPAN = 32*ROX_K consecutive grid points
+// (each lane ROX_K points strided by 32) and is its own unit of scheduling; CTAs of
+// ROX_WARPS warps only share the Dawson table. Lines reach a warp in batches of 32.
 #define ROX_WARPS 8
 #define ROX_THREADS (ROX_WARPS * 32)
 #define ROX_K 8
-#define ROX_TILE (ROX_THREADS * ROX_K)
-#define ROX_CHUNK ROX_THREADS            // lines staged per pass through shared memory
+#define ROX_SPAN (32 * ROX_K)
+#define ROX_TILE ROX_SPAN               // grid points per work item (per-item line ranges)
 
 // The far (2-level continued fraction) formula is used only for points with
 // x^2 + y^2 >= 22^2. Its per-point offset is X_m = X_0 + 32 m dnu with X_0 the offset at
@@ -53,7 +54,7 @@ struct RoxPt {
 
 struct RoxVoigtArgs {
   const float4* geo;        // [n_lines] {k0 (float, exact), f*dnu, jlo (int bits), jhi (int bits)}
-  const double* S_T;        // [n_temps][n_lines] line strength, FP64
+  const float* S32;         // [n_temps][n_lines] line strength * 2^-e_t (FP32; e_t from smax_bits)
   const void* gamma_ref;
   const void* n_t;
   int32_t width_f16;

@@ -80,6 +80,19 @@ __global__ void k_strengths_multi(rox_lines L, TempSet ts,
   }
 }
 
+// S * 2^-e per temperature, e the exponent of the largest strength at that temperature,
+// so the Voigt kernel works in FP32 well inside its range whatever the line strengths are.
+__global__ void k_scale_strengths(const double* __restrict__ S_T, long long n, int n_temps,
+                                  const unsigned long long* __restrict__ smax_bits, float* S32) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (int t = 0; t < n_temps; t++) {
+    double smax = __longlong_as_double((long long)smax_bits[t]);
+    double sc = ldexp(1.0, smax > 0.0 ? -ilogb(smax) : 0);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+      S32[(long long)t * n + i] = (float)(S_T[(long long)t * n + i] * sc);
+  }
+}
+
 StrengthConsts make_consts(int convention, double T, double Q_T, double Q_ref) {
   StrengthConsts k;
   k.convention = convention;
@@ -123,5 +136,11 @@ cudaError_t rox_launch_strengths_multi(const rox_lines* L, int n_temps, const do
   ts.n = n_temps;
   for (int t = 0; t < n_temps; t++) ts.k[t] = make_consts(L->convention, temps[t], q_of_temp[t], Q_ref);
   k_strengths_multi<<<grid_for(L->n), 256, 0, s>>>(*L, ts, S_T, smax_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_scale_strengths(const double* S_T, long long n, int n_temps,
+                                       const unsigned long long* smax_bits, float* S32, cudaStream_t s) {
+  k_scale_strengths<<<grid_for(n), 256, 0, s>>>(S_T, n, n_temps, smax_bits, S32);
   return cudaGetLastError();
 }

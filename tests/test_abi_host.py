@@ -69,7 +69,7 @@ def test_workspace_size_is_host_only(lib):
     G = lib.RoxGrid(300.0, 0.01, 2970001)
     a = lib.lib.rox_xsec_workspace_size(10_000_000, ctypes.byref(G), 1)
     b = lib.lib.rox_xsec_workspace_size(10_000_000, ctypes.byref(G), 20)
-    assert a > 10_000_000 * (16 + 8) and b - a == 19 * 10_000_000 * 8
+    assert a > 10_000_000 * (16 + 12) and b - a == 19 * 10_000_000 * 12   # FP64 + scaled FP32 strengths
     assert lib.lib.rox_xsec_workspace_size(10, ctypes.byref(G), 0) == 0
 
 
