@@ -193,6 +193,28 @@ int rox_ws_status(const void* ws, unsigned long long* evals_out, void* stream);
  * stream. Pass NULL, NULL to stop. Recording is stream-ordered and adds no sync. */
 int rox_set_profile_events(void* start, void* stop);
 
+/* Allocation-free variant of rox_xsec (one (P,T) point), for callers that cannot
+ * allocate device memory themselves: an application whose own memory manager owns all
+ * device memory, a plugin that is not allowed to call cudaMalloc, or an interface that
+ * has no way to pass a workspace through. The paper has no counterpart; this is a
+ * packaging convenience of this library.
+ * The scratch lives in one fixed array inside the library (8 MiB of device memory held on
+ * every GPU that loads the library, until the process exits), so sizes are limited to
+ * lines->n <= ROX_STATIC_MAX_LINES and grid->n <= ROX_STATIC_MAX_GRID; larger problems
+ * return ROX_ERANGE (use rox_xsec with a workspace). Arguments and results are those of
+ * rox_xsec; status_out (device, 1 x int32, may be NULL) receives the call's device-side
+ * status (ROX_OK, or ROX_EUNSORTED with sigma_out untouched), stream-ordered.
+ * No cudaMalloc, cudaFree or other allocation is made. The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. All calls share the one array: calls that overlap on the GPU (different
+ * streams, or different host threads, on one device) race and corrupt each other's results;
+ * serialise them. Each call clears the parts of the array that must start at zero. */
+#define ROX_STATIC_MAX_LINES 262144
+#define ROX_STATIC_MAX_GRID (1 << 21)
+int rox_xsec_static(const rox_lines* lines, const rox_grid* grid, double P_bar, double T, double Q_T,
+                    double Q_ref, double mass_amu, double cutoff, float* sigma_out, int32_t* status_out,
+                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,10 +8,10 @@ library has not been built: there is no CPU fallback.
 from ._binding import (ROX_ACCUMULATE, ROX_EXOMOL, ROX_HITRAN, ROX_MAX_PT, ROX_TILE, RoxError, lib, version,
                        rox_faddeeva_re, rox_line_strengths, rox_line_widths, rox_line_windows, rox_set_profile_events, rox_sort_lines,
                        rox_sort_workspace_size, rox_tile_ranges, rox_ws_status, rox_xsec, rox_xsec_batch,
-                       rox_xsec_workspace_size)
+                       rox_xsec_static, rox_xsec_workspace_size)
 from .partition import PartitionFunction
 
 __all__ = ["ROX_ACCUMULATE", "ROX_EXOMOL", "ROX_HITRAN", "ROX_MAX_PT", "ROX_TILE", "RoxError", "lib", "version",
            "rox_faddeeva_re", "rox_line_strengths", "rox_line_widths", "rox_line_windows", "rox_set_profile_events", "rox_sort_lines",
            "rox_sort_workspace_size", "rox_tile_ranges", "rox_ws_status", "rox_xsec", "rox_xsec_batch",
-           "rox_xsec_workspace_size", "PartitionFunction"]
+           "rox_xsec_static", "rox_xsec_workspace_size", "PartitionFunction"]

@@ -63,6 +63,7 @@ def _load():
         "rox_xsec": (ctypes.c_int, [P, P, D, D, D, D, D, D, P, P, ctypes.c_size_t, P]),
         "rox_ws_status": (ctypes.c_int, [P, P, P]),
         "rox_set_profile_events": (ctypes.c_int, [P, P]),
+        "rox_xsec_static": (ctypes.c_int, [P, P, D, D, D, D, D, D, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -183,6 +184,14 @@ def rox_set_profile_events(start=None, stop=None):
     CUDA event exists) or None to disable."""
     h = (lambda e: None if e is None else ctypes.c_void_p(e.cuda_event))
     _check(lib.rox_set_profile_events(h(start), h(stop)))
+
+
+def rox_xsec_static(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, status_out=None, stream=None):
+    """rox_xsec without a workspace (scratch held by the library; see include/rox.h)."""
+    L = lines_struct(lines)
+    G = grid_struct(grid)
+    _check(lib.rox_xsec_static(ctypes.byref(L), ctypes.byref(G), P_bar, T, Q_T, Q_ref, mass_amu, cutoff,
+                               _ptr(sigma_out), _ptr(status_out), _stream(stream)))
 
 
 def rox_ws_status(ws, stream=None):

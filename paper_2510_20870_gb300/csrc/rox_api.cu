@@ -150,6 +150,9 @@ int voigt_grid(int* out) {
 
 }  // namespace
 
+// sets this thread's error message for entry points defined in other translation units
+int rox_set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 const char* rox_last_error(void) { return g_err.c_str(); }
