@@ -5,7 +5,7 @@ Run: python gen_faddeeva_tables.py > rox_faddeeva_tables.h  (build() checks it i
 Everything is derived here from mathematics, with exact rational arithmetic where
 it matters; no special-function library is called:
   * Taylor coefficients of Dawson's integral F(x) = exp(-x^2) int_0^x exp(t^2) dt
-    around nodes x_c = 0, 0.25, ..., 6.0, from its Maclaurin series
+    around nodes x_c = 0, 0.125, ..., 6.0, from its Maclaurin series
     F(x) = sum_k (-1)^k 2^k x^(2k+1) / (2k+1)!!  (exact rationals, summed to 1e-60)
     and the ODE F' = 1 - 2 x F, which gives (n+1) d_{n+1} = [n=0] - 2 x_c d_n - 2 d_{n-1}.
   * Weideman's rational approximation (J.A.C. Weideman, SIAM J. Numer. Anal. 31 (1994)
@@ -19,9 +19,9 @@ it matters; no special-function library is called:
 from fractions import Fraction as Fr
 import numpy as np
 
-DAW_STEP = Fr(1, 4)      # node spacing
-DAW_NODES = 25           # x_c = 0 .. 6.0
-DAW_DEG = 12
+DAW_STEP = Fr(1, 8)      # node spacing
+DAW_NODES = 49           # x_c = 0 .. 6.0
+DAW_DEG = 7
 WEI_N = 20
 
 
