@@ -187,6 +187,48 @@ int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double 
  * call's (P,T) points (the unit of work of the Voigt kernel). */
 int rox_ws_status(const void* ws, unsigned long long* evals_out, void* stream);
 
+/* Serving path, a3 once per list: a sorted line list prepared on a lattice (a grid shared by
+ * all requests on it) -- its cutoff windows and its line range per lattice span of ROX_SPAN
+ * points -- for any number of rox_xsec_jobs calls with output windows on that lattice.
+ * state: device memory of rox_prepare_size(n, lattice) bytes, owned by the caller and kept
+ * while `out` is in use. rox_ws_status(state, ...) reports ROX_EUNSORTED if nu0 was not
+ * ascending (jobs on such a list then leave their output untouched). */
+#define ROX_SPAN 256
+typedef struct rox_prepared {
+  rox_lines lines;
+  rox_grid lattice;
+  double cutoff;
+  void* state;
+  const int64_t* span_lo;   /* device [n_spans]: first line reaching lattice span s */
+  const int64_t* span_hi;   /* device [n_spans]: one past the last line reaching span s */
+  int64_t n_spans;
+} rox_prepared;
+size_t rox_prepare_size(int64_t n_lines, const rox_grid* lattice);
+int rox_prepare(const rox_lines* lines, const rox_grid* lattice, double cutoff, void* state, size_t state_bytes,
+                rox_prepared* out, void* stream);
+
+/* One cross-section request: a window of lattice points on one prepared list at one (P,T).
+ * line_first/line_count give the lines that can reach the window, read from a host copy of
+ * the list's span tables: line_first = span_lo[first / ROX_SPAN], line_count =
+ * span_hi[(first + n - 1) / ROX_SPAN] - line_first; lines outside the range are skipped. */
+typedef struct rox_job {
+  int32_t list;               /* index into the `lists` of rox_xsec_jobs */
+  uint32_t flags;             /* 0 or ROX_ACCUMULATE */
+  int64_t first, n;           /* lattice points [first, first + n) */
+  int64_t line_first, line_count;
+  double P_bar, T, Q_T, Q_ref, mass_amu;
+  float* sigma_out;           /* [n] float (device) */
+} rox_job;
+
+/* a1 + a4 for many requests in one persistent launch (continuous-batching server, batched
+ * windows): per job the strengths of its line range at its T (FP64, then scaled to FP32),
+ * then one Voigt launch over all (job, span) items. Each job's result is independent of the
+ * others in the launch (same summation order as alone). n_jobs <= ROX_MAX_PT,
+ * n_lists <= 8. ws: rox_jobs_workspace_size(jobs, n_jobs) bytes. */
+size_t rox_jobs_workspace_size(const rox_job* jobs, int n_jobs);
+int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, int n_jobs, void* ws, size_t ws_bytes,
+                  void* stream);
+
 /* Measurement hook: when start/stop are not NULL (cudaEvent_t handles created by the
  * caller), every following rox_xsec / rox_xsec_batch call on this thread records `start`
  * just before and `stop` just after its Voigt-accumulate kernel launch, on the call's

@@ -42,6 +42,18 @@ class RoxGrid(ctypes.Structure):
     _fields_ = [("nu_min", ctypes.c_double), ("dnu", ctypes.c_double), ("n", ctypes.c_int64)]
 
 
+class RoxPrepared(ctypes.Structure):
+    _fields_ = [("lines", RoxLines), ("lattice", RoxGrid), ("cutoff", ctypes.c_double), ("state", ctypes.c_void_p),
+                ("span_lo", ctypes.c_void_p), ("span_hi", ctypes.c_void_p), ("n_spans", ctypes.c_int64)]
+
+
+class RoxJob(ctypes.Structure):
+    _fields_ = [("list", ctypes.c_int32), ("flags", ctypes.c_uint32), ("first", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("line_first", ctypes.c_int64), ("line_count", ctypes.c_int64), ("P_bar", ctypes.c_double),
+                ("T", ctypes.c_double), ("Q_T", ctypes.c_double), ("Q_ref", ctypes.c_double),
+                ("mass_amu", ctypes.c_double), ("sigma_out", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("librox.so is not built: run `python -c \"import __graft_entry__ as g; g.build()\"` "
@@ -64,6 +76,10 @@ def _load():
         "rox_ws_status": (ctypes.c_int, [P, P, P]),
         "rox_set_profile_events": (ctypes.c_int, [P, P]),
         "rox_xsec_static": (ctypes.c_int, [P, P, D, D, D, D, D, D, P, P, P]),
+        "rox_prepare_size": (ctypes.c_size_t, [I64, P]),
+        "rox_prepare": (ctypes.c_int, [P, P, D, P, ctypes.c_size_t, P, P]),
+        "rox_jobs_workspace_size": (ctypes.c_size_t, [P, ctypes.c_int]),
+        "rox_xsec_jobs": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -192,6 +208,65 @@ def rox_xsec_static(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_o
     G = grid_struct(grid)
     _check(lib.rox_xsec_static(ctypes.byref(L), ctypes.byref(G), P_bar, T, Q_T, Q_ref, mass_amu, cutoff,
                                _ptr(sigma_out), _ptr(status_out), _stream(stream)))
+
+
+ROX_SPAN = 256
+
+
+class Prepared:
+    """A sorted line list prepared on a lattice for rox_xsec_jobs (keeps its buffers alive).
+    span_lo / span_hi: host copies of the per-span line ranges (numpy int64)."""
+
+    def __init__(self, lines, lattice, cutoff, stream=None):
+        import numpy as np
+        self.lines = lines
+        self.lattice = tuple(lattice)
+        self.cutoff = float(cutoff)
+        n = lines["nu0"].numel()
+        G = grid_struct(lattice)
+        self.state = torch.empty(lib.rox_prepare_size(n, ctypes.byref(G)), dtype=torch.uint8,
+                                 device=lines["nu0"].device)
+        self.struct = RoxPrepared()
+        L = lines_struct(lines)
+        _check(lib.rox_prepare(ctypes.byref(L), ctypes.byref(G), self.cutoff, _ptr(self.state), self.state.numel(),
+                               ctypes.byref(self.struct), _stream(stream)))
+        ns = self.struct.n_spans
+        lo = torch.empty(ns, dtype=torch.int64, device=self.state.device)
+        hi = torch.empty(ns, dtype=torch.int64, device=self.state.device)
+        dev = self.state.device
+        # copy the device span tables (views of the state buffer) to host once
+        off_lo = self.struct.span_lo - self.state.data_ptr()
+        off_hi = self.struct.span_hi - self.state.data_ptr()
+        lo.copy_(self.state[off_lo:off_lo + 8 * ns].view(torch.int64))
+        hi.copy_(self.state[off_hi:off_hi + 8 * ns].view(torch.int64))
+        self.span_lo = lo.cpu().numpy()
+        self.span_hi = hi.cpu().numpy()
+        self.n_lines = n
+
+    def line_range(self, first, n):
+        s0, s1 = first // ROX_SPAN, (first + n - 1) // ROX_SPAN
+        l0 = int(self.span_lo[s0])
+        return l0, max(0, int(self.span_hi[s1]) - l0)
+
+    def status(self, stream=None):
+        return rox_ws_status(self.state, stream)
+
+
+def make_job(prepared, list_index, first, n, P_bar, T, Q_T, Q_ref, mass_amu, sigma_out, flags=0):
+    l0, cnt = prepared.line_range(first, n)
+    return RoxJob(list=list_index, flags=flags, first=first, n=n, line_first=l0, line_count=cnt, P_bar=P_bar, T=T,
+                  Q_T=Q_T, Q_ref=Q_ref, mass_amu=mass_amu, sigma_out=_ptr(sigma_out).value)
+
+
+def rox_jobs_workspace_size(jobs):
+    arr = (RoxJob * len(jobs))(*jobs)
+    return lib.rox_jobs_workspace_size(arr, len(jobs))
+
+
+def rox_xsec_jobs(prepared_lists, jobs, ws, stream=None):
+    lists = (RoxPrepared * len(prepared_lists))(*[p.struct for p in prepared_lists])
+    arr = (RoxJob * len(jobs))(*jobs)
+    _check(lib.rox_xsec_jobs(lists, len(prepared_lists), arr, len(jobs), _ptr(ws), ws.numel(), _stream(stream)))
 
 
 def rox_ws_status(ws, stream=None):

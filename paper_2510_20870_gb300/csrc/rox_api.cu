@@ -31,6 +31,8 @@ size_t rox_sort_ws_bytes(long long n);
 cudaError_t rox_launch_sort(const rox_lines* in, const rox_lines_buf* out, int64_t* perm_out, void* ws,
                             cudaStream_t s);
 cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, cudaStream_t s);
+void rox_fill_strength_consts(int convention, double T, double Q_T, double Q_ref, RoxStrengthJob* jb);
+cudaError_t rox_launch_strengths_jobs(const RoxStrengthJobs& J, long long max_count, cudaStream_t s);
 cudaError_t rox_voigt_blocks_per_sm(int* nb);
 cudaError_t rox_launch_faddeeva(const float* x, const float* y, float* out, long long n, cudaStream_t s);
 
@@ -145,6 +147,33 @@ int voigt_grid(int* out) {
     g_voigt_device = dev;
   }
   *out = g_voigt_blocks;
+  return ROX_OK;
+}
+
+// Voigt launches over the jobs, at most ROX_MAX_JOBS per launch; the work counter is reset
+// before each launch (the evaluation count keeps adding up).
+int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* jobs, int n_jobs, RoxWsHeader* hdr,
+                      int nblocks, cudaStream_t s) {
+  static thread_local RoxVoigtArgs A;   // ~30 KB of per-job parameters, passed by value
+  A.hdr = hdr;
+  for (int l = 0; l < n_lists; l++) A.list[l] = lists[l];
+  for (int j0 = 0; j0 < n_jobs; j0 += ROX_MAX_JOBS) {
+    const int nj = (n_jobs - j0) < ROX_MAX_JOBS ? (n_jobs - j0) : ROX_MAX_JOBS;
+    int items = 0;
+    for (int k = 0; k < nj; k++) {
+      A.job[k] = jobs[j0 + k];
+      items += A.job[k].n_spans;
+      A.item_end[k] = items;
+    }
+    A.n_jobs = nj;
+    A.n_items = items;
+    int rc;
+    if ((rc = cuda_check(cudaMemsetAsync(&hdr->work_counter, 0, sizeof(int32_t), s), "memset"))) return rc;
+    if (j0 == 0 && g_prof_start && (rc = cuda_check(cudaEventRecord(g_prof_start, s), "cudaEventRecord"))) return rc;
+    if (items == 0) continue;
+    if ((rc = cuda_check(rox_launch_voigt(A, items < nblocks ? items : nblocks, s), "voigt kernel"))) return rc;
+  }
+  if (g_prof_stop) return cuda_check(cudaEventRecord(g_prof_stop, s), "cudaEventRecord");
   return ROX_OK;
 }
 
@@ -275,31 +304,6 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
   const long long nt = n_tiles_of(grid->n);
   const long long nl = lines->n;
 
-  static thread_local RoxVoigtArgs A;   // 8 KB of per-point parameters, passed by value
-  A.geo = w.geo;
-  A.S32 = w.S32;
-  A.gamma_ref = lines->gamma_ref;
-  A.n_t = lines->n_t;
-  A.width_f16 = lines->width_dtype == ROX_WIDTH_F16;
-  A.tile_lo = w.tlo;
-  A.tile_hi = w.thi;
-  A.n_tiles = (int32_t)nt;
-  A.n_pt = n_pt;
-  A.n_lines = nl;
-  A.n_grid = grid->n;
-  A.nu_min = grid->nu_min;
-  A.dnu_f = (float)grid->dnu;
-  A.nu_min_f = (float)grid->nu_min;
-  A.hdr = w.hdr;
-  A.sigma = sigma_out;
-  A.flags = flags;
-  for (int k = 0; k < n_pt; k++) {
-    A.pt[k].p_fac = (float)(P_bar[k] / ROX_P_REF);
-    A.pt[k].gG_fac = (float)(sqrt(2.0 * ROX_KB * T[k] / (mass_amu * ROX_AMU)) / ROX_C_M);
-    A.pt[k].l2_ratio = (float)log2(ROX_T_REF / T[k]);
-    A.pt[k].t_idx = tidx[k];
-  }
-
   if ((rc = cuda_check(cudaMemsetAsync(w.hdr, 0, sizeof(RoxWsHeader), s), "memset"))) return rc;
   if (nl > 0) {
     if ((rc = cuda_check(rox_launch_windows(lines->nu0, nl, grid, cutoff, nullptr, nullptr, nullptr, nullptr, w.geo,
@@ -316,11 +320,38 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
   }
   if ((rc = cuda_check(rox_launch_tile_ranges_geo(w.geo, nl, nt, ROX_TILE, w.tlo, w.thi, s), "tile ranges")))
     return rc;
-  long long items = (long long)n_pt * nt;
-  int grid_blocks = (int)(items < nblocks ? items : nblocks);
-  if (g_prof_start && (rc = cuda_check(cudaEventRecord(g_prof_start, s), "cudaEventRecord"))) return rc;
-  if ((rc = cuda_check(rox_launch_voigt(A, grid_blocks, s), "voigt kernel"))) return rc;
-  if (g_prof_stop && (rc = cuda_check(cudaEventRecord(g_prof_stop, s), "cudaEventRecord"))) return rc;
+  RoxListDev L0;
+  L0.status = &w.hdr->status;
+  L0.geo = w.geo;
+  L0.span_lo = w.tlo;
+  L0.span_hi = w.thi;
+  L0.gamma_ref = lines->gamma_ref;
+  L0.n_t = lines->n_t;
+  L0.n_lattice = grid->n;
+  L0.dnu_f = (float)grid->dnu;
+  L0.nu_min_f = (float)grid->nu_min;
+  L0.width_f16 = lines->width_dtype == ROX_WIDTH_F16;
+  L0.pad = 0;
+  std::vector<RoxJobDev> jobs(n_pt);
+  for (int k = 0; k < n_pt; k++) {
+    RoxJobDev& J = jobs[k];
+    J.S32 = w.S32 + (size_t)tidx[k] * (size_t)(nl > 0 ? nl : 1);
+    J.sigma = sigma_out + (size_t)k * (size_t)grid->n;
+    J.smax_bits = &w.hdr->smax_bits[tidx[k]];
+    J.l0 = 0;
+    J.l1 = nl;
+    J.first = 0;
+    J.n = grid->n;
+    J.list = 0;
+    J.span_first = 0;
+    J.n_spans = (int32_t)nt;
+    J.p_fac = (float)(P_bar[k] / ROX_P_REF);
+    J.gG_fac = (float)(sqrt(2.0 * ROX_KB * T[k] / (mass_amu * ROX_AMU)) / ROX_C_M);
+    J.l2_ratio = (float)log2(ROX_T_REF / T[k]);
+    J.flags = flags;
+    J.pad = 0;
+  }
+  if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, nblocks, s))) return rc;
   return ok();
 }
 
@@ -328,6 +359,194 @@ int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double 
              double mass_amu, double cutoff, float* sigma_out, void* ws, size_t ws_bytes, void* stream) {
   return rox_xsec_batch(lines, grid, 1, &P_bar, &T, &Q_T, Q_ref, mass_amu, cutoff, 0u, sigma_out, ws, ws_bytes,
                         stream);
+}
+
+// ---------------------------------------------------------------- serving path
+namespace {
+struct PrepLayout {
+  RoxWsHeader* hdr;
+  float4* geo;
+  long long* span_lo;
+  long long* span_hi;
+  size_t bytes;
+};
+PrepLayout prep_layout(void* state, long long n_lines, long long n_lattice) {
+  PrepLayout p;
+  char* base = (char*)state;
+  size_t off = 0;
+  p.hdr = (RoxWsHeader*)base;
+  off += ROX_WS_HEADER_BYTES;
+  p.geo = (float4*)(base + off);
+  off += rox_align256((size_t)(n_lines > 0 ? n_lines : 1) * sizeof(float4));
+  long long ns = n_tiles_of(n_lattice);
+  p.span_lo = (long long*)(base + off);
+  off += rox_align256((size_t)ns * 8);
+  p.span_hi = (long long*)(base + off);
+  off += rox_align256((size_t)ns * 8);
+  p.bytes = off;
+  return p;
+}
+}  // namespace
+
+size_t rox_prepare_size(int64_t n_lines, const rox_grid* lattice) {
+  if (!lattice || lattice->n <= 0 || n_lines < 0) return 0;
+  return prep_layout(nullptr, n_lines, lattice->n).bytes;
+}
+
+int rox_prepare(const rox_lines* lines, const rox_grid* lattice, double cutoff, void* state, size_t state_bytes,
+                rox_prepared* out, void* stream) {
+  int rc = check_lines(lines, true, true);
+  if (rc) return rc;
+  if ((rc = check_grid(lattice))) return rc;
+  if ((rc = check_cutoff(cutoff, lattice))) return rc;
+  if (!out) return fail(ROX_EINVAL, "out is NULL");
+  if (!state || ((uintptr_t)state & 255)) return fail(ROX_EINVAL, "state NULL or not 256-byte aligned");
+  PrepLayout p = prep_layout(state, lines->n, lattice->n);
+  if (state_bytes < p.bytes) return fail(ROX_ENOMEM, "state %zu bytes < %zu needed", state_bytes, p.bytes);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long ns = n_tiles_of(lattice->n);
+  if ((rc = cuda_check(cudaMemsetAsync(p.hdr, 0, sizeof(RoxWsHeader), s), "memset"))) return rc;
+  if (lines->n > 0 &&
+      (rc = cuda_check(rox_launch_windows(lines->nu0, lines->n, lattice, cutoff, nullptr, nullptr, nullptr, nullptr,
+                                          p.geo, &p.hdr->evals_lines, &p.hdr->status, ROX_EUNSORTED, s),
+                       "windows kernel")))
+    return rc;
+  if ((rc = cuda_check(rox_launch_tile_ranges_geo(p.geo, lines->n, ns, ROX_SPAN, p.span_lo, p.span_hi, s),
+                       "span ranges")))
+    return rc;
+  out->lines = *lines;
+  out->lattice = *lattice;
+  out->cutoff = cutoff;
+  out->state = state;
+  out->span_lo = (const int64_t*)p.span_lo;
+  out->span_hi = (const int64_t*)p.span_hi;
+  out->n_spans = ns;
+  return ok();
+}
+
+namespace {
+size_t jobs_layout(const rox_job* jobs, int n_jobs, void* ws, double** S64, float** S32) {
+  size_t off = ROX_WS_HEADER_BYTES;
+  for (int k = 0; k < n_jobs; k++) {
+    const size_t c = (size_t)(jobs[k].line_count > 0 ? jobs[k].line_count : 1);
+    if (S64) S64[k] = (double*)((char*)ws + off);
+    off += rox_align256(c * 8);
+    if (S32) S32[k] = (float*)((char*)ws + off);
+    off += rox_align256(c * 4);
+  }
+  return off;
+}
+}  // namespace
+
+size_t rox_jobs_workspace_size(const rox_job* jobs, int n_jobs) {
+  if (!jobs || n_jobs <= 0) return 0;
+  return jobs_layout(jobs, n_jobs, nullptr, nullptr, nullptr);
+}
+
+int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, int n_jobs, void* ws, size_t ws_bytes,
+                  void* stream) {
+  if (!lists || n_lists < 1 || n_lists > ROX_MAX_LISTS) return fail(ROX_EINVAL, "n_lists must be 1..%d", ROX_MAX_LISTS);
+  if (!jobs || n_jobs < 1 || n_jobs > ROX_MAX_PT) return fail(ROX_EINVAL, "n_jobs must be 1..%d", ROX_MAX_PT);
+  int rc;
+  for (int l = 0; l < n_lists; l++) {
+    if ((rc = check_lines(&lists[l].lines, true, true))) return rc;
+    if (!lists[l].state || !lists[l].span_lo || !lists[l].span_hi) return fail(ROX_EINVAL, "list %d not prepared", l);
+  }
+  for (int k = 0; k < n_jobs; k++) {
+    const rox_job& j = jobs[k];
+    if (j.list < 0 || j.list >= n_lists) return fail(ROX_EINVAL, "job %d: list %d out of range", k, j.list);
+    const rox_prepared& L = lists[j.list];
+    if (j.n <= 0 || j.first < 0 || j.first + j.n > L.lattice.n)
+      return fail(ROX_EINVAL, "job %d: window [%lld, %lld) outside the lattice", k, (long long)j.first,
+                  (long long)(j.first + j.n));
+    if (j.line_first < 0 || j.line_count < 0 || j.line_first + j.line_count > L.lines.n)
+      return fail(ROX_EINVAL, "job %d: line range outside the list", k);
+    if (!finite_pos(j.T) || !finite_pos(j.Q_T) || !finite_pos(j.Q_ref) || !finite_pos(j.mass_amu) ||
+        !std::isfinite(j.P_bar) || j.P_bar < 0)
+      return fail(ROX_EINVAL, "job %d: T, Q_T, Q_ref, mass > 0 and P >= 0 required", k);
+    if (j.flags & ~ROX_ACCUMULATE) return fail(ROX_EINVAL, "job %d: unknown flags", k);
+    if (!j.sigma_out) return fail(ROX_EINVAL, "job %d: sigma_out is NULL", k);
+  }
+  if (!ws || ((uintptr_t)ws & 255)) return fail(ROX_EINVAL, "workspace NULL or not 256-byte aligned");
+  const size_t need = jobs_layout(jobs, n_jobs, nullptr, nullptr, nullptr);
+  if (ws_bytes < need) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
+  int nblocks = 0;
+  if ((rc = voigt_grid(&nblocks))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  RoxWsHeader* hdr = (RoxWsHeader*)ws;
+  std::vector<double*> S64(n_jobs);
+  std::vector<float*> S32(n_jobs);
+  jobs_layout(jobs, n_jobs, ws, S64.data(), S32.data());
+  if ((rc = cuda_check(cudaMemsetAsync(hdr, 0, sizeof(RoxWsHeader), s), "memset"))) return rc;
+
+  // strengths of every job's line range at its temperature
+  static thread_local RoxStrengthJobs SJ;
+  for (int l = 0; l < n_lists; l++) {
+    SJ.list[l].nu0 = lists[l].lines.nu0;
+    SJ.list[l].s_or_a = lists[l].lines.s_or_a;
+    SJ.list[l].g_up = lists[l].lines.g_up;
+    SJ.list[l].e_lower = lists[l].lines.e_lower;
+    SJ.list[l].convention = lists[l].lines.convention;
+    SJ.list[l].pad = 0;
+  }
+  for (int j0 = 0; j0 < n_jobs; j0 += ROX_MAX_JOBS) {
+    const int nj = (n_jobs - j0) < ROX_MAX_JOBS ? (n_jobs - j0) : ROX_MAX_JOBS;
+    long long mx = 1;
+    for (int q = 0; q < nj; q++) {
+      const rox_job& j = jobs[j0 + q];
+      RoxStrengthJob& jb = SJ.job[q];
+      jb.l0 = j.line_first;
+      jb.count = j.line_count;
+      jb.S64 = S64[j0 + q];
+      jb.S32 = S32[j0 + q];
+      jb.smax_bits = &hdr->smax_bits[j0 + q];
+      jb.list = j.list;
+      jb.pad = 0;
+      rox_fill_strength_consts(lists[j.list].lines.convention, j.T, j.Q_T, j.Q_ref, &jb);
+      if (j.line_count > mx) mx = j.line_count;
+    }
+    SJ.n_jobs = nj;
+    if ((rc = cuda_check(rox_launch_strengths_jobs(SJ, mx, s), "strengths kernel"))) return rc;
+  }
+
+  // one Voigt launch over all (job, span) items
+  RoxListDev L[ROX_MAX_LISTS];
+  for (int l = 0; l < n_lists; l++) {
+    const rox_prepared& P = lists[l];
+    L[l].status = &((RoxWsHeader*)P.state)->status;
+    L[l].geo = (const float4*)((char*)P.state + ROX_WS_HEADER_BYTES);
+    L[l].span_lo = (const long long*)P.span_lo;
+    L[l].span_hi = (const long long*)P.span_hi;
+    L[l].gamma_ref = P.lines.gamma_ref;
+    L[l].n_t = P.lines.n_t;
+    L[l].n_lattice = P.lattice.n;
+    L[l].dnu_f = (float)P.lattice.dnu;
+    L[l].nu_min_f = (float)P.lattice.nu_min;
+    L[l].width_f16 = P.lines.width_dtype == ROX_WIDTH_F16;
+    L[l].pad = 0;
+  }
+  std::vector<RoxJobDev> J(n_jobs);
+  for (int k = 0; k < n_jobs; k++) {
+    const rox_job& j = jobs[k];
+    RoxJobDev& d = J[k];
+    d.S32 = S32[k];
+    d.sigma = j.sigma_out;
+    d.smax_bits = &hdr->smax_bits[k];
+    d.l0 = j.line_first;
+    d.l1 = j.line_first + j.line_count;
+    d.first = j.first;
+    d.n = j.n;
+    d.list = j.list;
+    d.span_first = (int32_t)(j.first / ROX_SPAN);
+    d.n_spans = (int32_t)((j.first + j.n - 1) / ROX_SPAN - j.first / ROX_SPAN + 1);
+    d.p_fac = (float)(j.P_bar / ROX_P_REF);
+    d.gG_fac = (float)(sqrt(2.0 * ROX_KB * j.T / (j.mass_amu * ROX_AMU)) / ROX_C_M);
+    d.l2_ratio = (float)log2(ROX_T_REF / j.T);
+    d.flags = j.flags;
+    d.pad = 0;
+  }
+  if ((rc = launch_voigt_jobs(L, n_lists, J.data(), n_jobs, hdr, nblocks, s))) return rc;
+  return ok();
 }
 
 int rox_set_profile_events(void* start, void* stop) {

@@ -20,8 +20,7 @@
 // ROX_WARPS warps only share the Dawson table. Lines reach a warp in batches of 32.
 #define ROX_WARPS 8
 #define ROX_THREADS (ROX_WARPS * 32)
-#define ROX_K 8
-#define ROX_SPAN (32 * ROX_K)
+#define ROX_K (ROX_SPAN / 32)           // ROX_SPAN (include/rox.h) = 256 grid points per span
 #define ROX_TILE ROX_SPAN               // grid points per work item (per-item line ranges)
 
 // The far (2-level continued fraction) formula is used only for points with
@@ -32,45 +31,89 @@
 #define ROX_FAR_Z2 484.0
 #define ROX_FAST_MARGIN 0.032
 
-// Workspace header at the start of every xsec workspace.
+// Workspace header at the start of every xsec / prepared-list workspace.
 struct RoxWsHeader {
   int32_t status;                  // ROX_OK / ROX_EUNSORTED / ROX_ETIMEOUT
   int32_t n_pt;
-  unsigned long long evals_lines;  // (line, point) pairs inside the cutoff, one (P,T)
-  unsigned long long evals_total;  // evals_lines * n_pt, written by the Voigt kernel
+  unsigned long long evals_lines;  // (line, point) pairs inside the cutoff on the whole lattice
+  unsigned long long evals_total;  // pairs evaluated by the last Voigt launch(es), all jobs
   int32_t work_counter;            // persistent-kernel work queue
   int32_t pad;
-  unsigned long long smax_bits[ROX_MAX_PT];  // per distinct temperature: max S (double bits)
+  unsigned long long smax_bits[ROX_MAX_PT];  // per strength row: max S (double bits)
 };
 #define ROX_WS_HEADER_BYTES 8192
 
-// Per (P,T) point parameters of the Voigt kernel.
-struct RoxPt {
+// Voigt launch: up to ROX_MAX_LISTS prepared line lists and ROX_MAX_JOBS jobs, each job one
+// output window on its list's lattice at one (P,T) point; work items are (job, span) pairs.
+#define ROX_MAX_JOBS 320
+#define ROX_MAX_LISTS 8
+
+struct RoxListDev {
+  const int32_t* status;      // the list's preparation status (ROX_OK unless its nu0 was unsorted)
+  const float4* geo;          // [n_lines] {k0 (float, exact), f*dnu, jlo (int bits), jhi (int bits)}
+  const long long* span_lo;   // per lattice span of ROX_SPAN points: first line reaching it
+  const long long* span_hi;   //   and one past the last
+  const void* gamma_ref;
+  const void* n_t;
+  long long n_lattice;
+  float dnu_f;
+  float nu_min_f;
+  int32_t width_f16;
+  int32_t pad;
+};
+
+struct RoxJobDev {
+  const float* S32;                      // S * 2^-e of lines l0, l0+1, ... at this job's T
+  float* sigma;                          // sigma[j - first] for lattice points j in [first, first + n)
+  const unsigned long long* smax_bits;   // this job's largest strength (double bits)
+  long long l0;
+  long long l1;                          // lines [l0, l1) have strengths (others are skipped)
+  long long first;
+  long long n;
+  int32_t list;
+  int32_t span_first;
+  int32_t n_spans;
   float p_fac;      // P / P_ref
   float gG_fac;     // sqrt(2 k T / (m amu)) / c  -> gamma_G = nu0 * gG_fac
   float l2_ratio;   // log2(T_ref / T)           -> (T_ref/T)^n_T = exp2(n_T * l2_ratio)
-  int32_t t_idx;    // row of S_T (distinct temperature index)
+  uint32_t flags;   // ROX_ACCUMULATE
+  uint32_t pad;
 };
 
 struct RoxVoigtArgs {
-  const float4* geo;        // [n_lines] {k0 (float, exact), f*dnu, jlo (int bits), jhi (int bits)}
-  const float* S32;         // [n_temps][n_lines] line strength * 2^-e_t (FP32; e_t from smax_bits)
-  const void* gamma_ref;
-  const void* n_t;
-  int32_t width_f16;
-  const long long* tile_lo; // [n_tiles]
-  const long long* tile_hi;
-  int32_t n_tiles;
-  int32_t n_pt;
-  long long n_lines;
-  long long n_grid;
-  double nu_min;
-  float dnu_f;
-  float nu_min_f;
   RoxWsHeader* hdr;
-  float* sigma;
-  unsigned flags;
-  RoxPt pt[ROX_MAX_PT];
+  int32_t n_jobs;
+  int32_t n_items;
+  int32_t item_end[ROX_MAX_JOBS];   // item_end[k] = spans of jobs 0..k
+  RoxListDev list[ROX_MAX_LISTS];
+  RoxJobDev job[ROX_MAX_JOBS];
 };
+static_assert(sizeof(RoxVoigtArgs) < 32000, "kernel parameter space");
+
+// Strengths of each job's line range at the job's temperature (rox_xsec_jobs).
+struct RoxStrengthList {
+  const double* nu0;
+  const float* s_or_a;
+  const float* g_up;
+  const float* e_lower;
+  int32_t convention;
+  int32_t pad;
+};
+struct RoxStrengthJob {
+  long long l0, count;     // lines [l0, l0 + count) of list `list`
+  double* S64;             // [count]
+  float* S32;              // [count], S * 2^-e of the job's maximum
+  unsigned long long* smax_bits;
+  double inv_T, q_ratio, c2_dT;
+  int32_t list;
+  int32_t pad;
+};
+struct RoxStrengthJobs {
+  int32_t n_jobs;
+  int32_t pad;
+  RoxStrengthList list[ROX_MAX_LISTS];
+  RoxStrengthJob job[ROX_MAX_JOBS];
+};
+static_assert(sizeof(RoxStrengthJobs) < 32000, "kernel parameter space");
 
 static inline size_t rox_align256(size_t b) { return (b + 255) & ~(size_t)255; }

@@ -93,6 +93,43 @@ __global__ void k_scale_strengths(const double* __restrict__ S_T, long long n, i
   }
 }
 
+// Per-job strengths (rox_xsec_jobs): each job's line range at its own temperature, the
+// per-job maximum, then the job's FP32 scaled copy (second kernel, after the maximum is known).
+__global__ void k_strengths_jobs(const __grid_constant__ RoxStrengthJobs J) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (int q = 0; q < J.n_jobs; q++) {
+    const RoxStrengthJob& jb = J.job[q];
+    const RoxStrengthList& L = J.list[jb.list];
+    StrengthConsts k;
+    k.convention = L.convention;
+    k.inv_T = jb.inv_T;
+    k.q_ratio = jb.q_ratio;
+    k.c2_dT = jb.c2_dT;
+    double mx = 0.0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < jb.count; t += stride) {
+      const long long i = jb.l0 + t;
+      const double g = (L.convention == ROX_EXOMOL) ? (double)L.g_up[i] : 1.0;
+      const double sv = line_strength(k, L.nu0[i], (double)L.s_or_a[i], g, (double)L.e_lower[i]);
+      jb.S64[t] = sv;
+      mx = fmax(mx, sv);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(jb.smax_bits, (unsigned long long)__double_as_longlong(mx));
+  }
+}
+
+__global__ void k_scale_jobs(const __grid_constant__ RoxStrengthJobs J) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (int q = 0; q < J.n_jobs; q++) {
+    const RoxStrengthJob& jb = J.job[q];
+    const double smax = __longlong_as_double((long long)*jb.smax_bits);
+    const double sc = ldexp(1.0, smax > 0.0 ? -ilogb(smax) : 0);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < jb.count; t += stride)
+      jb.S32[t] = (float)(jb.S64[t] * sc);
+  }
+}
+
 StrengthConsts make_consts(int convention, double T, double Q_T, double Q_ref) {
   StrengthConsts k;
   k.convention = convention;
@@ -136,6 +173,21 @@ cudaError_t rox_launch_strengths_multi(const rox_lines* L, int n_temps, const do
   ts.n = n_temps;
   for (int t = 0; t < n_temps; t++) ts.k[t] = make_consts(L->convention, temps[t], q_of_temp[t], Q_ref);
   k_strengths_multi<<<grid_for(L->n), 256, 0, s>>>(*L, ts, S_T, smax_bits);
+  return cudaGetLastError();
+}
+
+void rox_fill_strength_consts(int convention, double T, double Q_T, double Q_ref, RoxStrengthJob* jb) {
+  StrengthConsts k = make_consts(convention, T, Q_T, Q_ref);
+  jb->inv_T = k.inv_T;
+  jb->q_ratio = k.q_ratio;
+  jb->c2_dT = k.c2_dT;
+}
+
+cudaError_t rox_launch_strengths_jobs(const RoxStrengthJobs& J, long long max_count, cudaStream_t s) {
+  k_strengths_jobs<<<grid_for(max_count), 256, 0, s>>>(J);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_scale_jobs<<<grid_for(max_count), 256, 0, s>>>(J);
   return cudaGetLastError();
 }
 

@@ -114,7 +114,7 @@ __device__ __forceinline__ void slow_line(const Rec& rq, int Aw, int lane, float
   }
 }
 
-__global__ void __launch_bounds__(ROX_THREADS, 4) k_voigt(const __grid_constant__ RoxVoigtArgs A) {
+__global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant__ RoxVoigtArgs A) {
   __shared__ float4 s_geo[ROX_WARPS][2][32];
   __shared__ float s_S[ROX_WARPS][2][32];
   __shared__ Rec s_rec[ROX_WARPS][32];
@@ -127,31 +127,43 @@ __global__ void __launch_bounds__(ROX_THREADS, 4) k_voigt(const __grid_constant_
   if (tid == 0) s_status = *(volatile int32_t*)&A.hdr->status;
   __syncthreads();
   if (s_status != ROX_OK) return;   // e.g. unsorted input: leave sigma untouched
-  if (blockIdx.x == 0 && tid == 0) A.hdr->evals_total = A.hdr->evals_lines * (unsigned long long)A.n_pt;
 
   float4(*geo_st)[32] = s_geo[w];
   float(*S_st)[32] = s_S[w];
   Rec* rec = s_rec[w];
-  const int f16 = A.width_f16;
-  const float dnu_f = A.dnu_f;
-  const float margin_cm = ROX_FAST_MARGIN * 32.0f * (ROX_K - 1) * dnu_f;
-  const long long n_items = (long long)A.n_pt * A.n_tiles;
+  unsigned long long evals = 0;   // (line, point) pairs inside the cutoff and the job's window
 
   for (;;) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(&A.hdr->work_counter, 1);
+    int item = 0, k = 0;
+    if (lane == 0) {
+      item = atomicAdd(&A.hdr->work_counter, 1);
+      int lo_k = 0, hi_k = A.n_jobs - 1;           // first job with item_end > item
+      while (lo_k < hi_k) {
+        const int mid = (lo_k + hi_k) >> 1;
+        if (A.item_end[mid] > item) hi_k = mid; else lo_k = mid + 1;
+      }
+      k = lo_k;
+    }
     item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= n_items) break;
-    const int pt = (int)(item / A.n_tiles);
-    const int span = A.n_tiles - 1 - (int)(item % A.n_tiles);   // wide-line (high nu) spans first
-    const RoxPt P = A.pt[pt];
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (item >= A.n_items) break;
+    const RoxJobDev& J = A.job[k];
+    const RoxListDev& Lst = A.list[J.list];
+    const int local = item - (k > 0 ? A.item_end[k - 1] : 0);
+    const int span = J.span_first + J.n_spans - 1 - local;       // wide-line (high nu) spans first
+    const int f16 = Lst.width_f16;
+    const float dnu_f = Lst.dnu_f;
+    const float margin_cm = ROX_FAST_MARGIN * 32.0f * (ROX_K - 1) * dnu_f;
     const int Aw = span * ROX_SPAN;
     const int Bw = Aw + ROX_SPAN - 1;
     const float Jf = (float)(Aw + lane);
-    const long long lo = A.tile_lo[span], hi = A.tile_hi[span];
-    const double smax = __longlong_as_double((long long)A.hdr->smax_bits[P.t_idx]);
-    const int e = smax > 0.0 ? ilogb(smax) : 0;     // S_row holds S * 2^-e (FP32)
-    const float* S_row = A.S32 + (long long)P.t_idx * A.n_lines;
+    if (*Lst.status != ROX_OK) continue;           // list not prepared from sorted lines
+    const long long lo = max(Lst.span_lo[span], J.l0), hi = min(Lst.span_hi[span], J.l1);
+    const long long wlo = J.first > Aw ? J.first : Aw;             // evaluated points of this span
+    const long long whi = (J.first + J.n - 1) < Bw ? (J.first + J.n - 1) : Bw;
+    const double smax = __longlong_as_double((long long)*J.smax_bits);
+    const int e = smax > 0.0 ? ilogb(smax) : 0;     // S32 holds S * 2^-e (FP32)
+    const float* S_row = J.S32 - J.l0;              // indexed by line number
 
     float acc[ROX_K], tot[ROX_K], cmp[ROX_K];
 #pragma unroll
@@ -160,10 +172,10 @@ __global__ void __launch_bounds__(ROX_THREADS, 4) k_voigt(const __grid_constant_
     // stage batch 0; widths go through registers one batch ahead
     float gref = 0.f, nt = 0.f;
     if (lo + lane < hi) {
-      cp_async16(&geo_st[0][lane], &A.geo[lo + lane]);
+      cp_async16(&geo_st[0][lane], &Lst.geo[lo + lane]);
       cp_async4(&S_st[0][lane], &S_row[lo + lane]);
-      gref = load_width(A.gamma_ref, f16, lo + lane);
-      nt = load_width(A.n_t, f16, lo + lane);
+      gref = load_width(Lst.gamma_ref, f16, lo + lane);
+      nt = load_width(Lst.n_t, f16, lo + lane);
     }
     cp_async_commit();
     int nb = 0;
@@ -172,10 +184,10 @@ __global__ void __launch_bounds__(ROX_THREADS, 4) k_voigt(const __grid_constant_
       const int buf = nb & 1;
       float gref_n = 0.f, nt_n = 0.f;
       if (b0 + 32 + lane < hi) {
-        cp_async16(&geo_st[buf ^ 1][lane], &A.geo[b0 + 32 + lane]);
+        cp_async16(&geo_st[buf ^ 1][lane], &Lst.geo[b0 + 32 + lane]);
         cp_async4(&S_st[buf ^ 1][lane], &S_row[b0 + 32 + lane]);
-        gref_n = load_width(A.gamma_ref, f16, b0 + 32 + lane);
-        nt_n = load_width(A.n_t, f16, b0 + 32 + lane);
+        gref_n = load_width(Lst.gamma_ref, f16, b0 + 32 + lane);
+        nt_n = load_width(Lst.n_t, f16, b0 + 32 + lane);
       }
       cp_async_commit();
       cp_async_wait1();   // this lane's copies of the current batch have landed
@@ -187,9 +199,11 @@ __global__ void __launch_bounds__(ROX_THREADS, 4) k_voigt(const __grid_constant_
         const float Sp = S_st[buf][lane];
         const int jlo = __float_as_int(g.z), jhi = __float_as_int(g.w);
         const int k0 = (int)g.x;
-        const float nu0f = A.nu_min_f + fmaf(g.x, dnu_f, g.y);
-        const float gG = nu0f * P.gG_fac;
-        const float gL = gref * exp2f(nt * P.l2_ratio) * P.p_fac;
+        const float nu0f = Lst.nu_min_f + fmaf(g.x, dnu_f, g.y);
+        const float gG = nu0f * J.gG_fac;
+        const float gL = gref * exp2f(nt * J.l2_ratio) * J.p_fac;
+        const long long ov = min((long long)jhi, whi) - max((long long)jlo, wlo) + 1;
+        if (ov > 0) evals += (unsigned long long)ov;
         const float gG2 = gG * gG, gL2 = gL * gL;
         const float pY = Sp * gL * ROX_INV_PI;
         const float invG = 1.0f / gG;
@@ -264,18 +278,21 @@ __global__ void __launch_bounds__(ROX_THREADS, 4) k_voigt(const __grid_constant_
       }
     }
     cp_async_wait0();
-    // ---- write the span once
-    float* out = A.sigma + (long long)pt * A.n_grid;
+    // ---- write the span once (its part inside the job's window)
+    float* out = J.sigma - J.first;
 #pragma unroll
     for (int m = 0; m < ROX_K; m++) {
       const long long j = (long long)Aw + 32 * m + lane;
-      if (j < A.n_grid) {
+      if (j >= wlo && j <= whi) {
         const float v = ldexpf(tot[m], e);
-        out[j] = (A.flags & ROX_ACCUMULATE) ? out[j] + v : v;
+        out[j] = (J.flags & ROX_ACCUMULATE) ? out[j] + v : v;
       }
     }
     __syncwarp();
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
+  if (lane == 0 && evals) atomicAdd(&A.hdr->evals_total, evals);
 }
 
 __global__ void k_faddeeva(const float* x, const float* y, float* out, long long n) {

@@ -39,13 +39,17 @@ def philox4x32_10(c0, c1, c2, c3, k0, k1):
     return c0, c1, c2, c3
 
 
-def uniform01(seed, stream, start, count):
-    """Doubles in the open interval (0, 1) for indices start..start+count-1.
+def uniform01(seed, stream, start, count, indices=None):
+    """Doubles in the open interval (0, 1) for indices start..start+count-1 (or the given
+    index array).
 
     Counter = (index low 32 bits, index high 32 bits, stream, 0), key = (seed, 0x524F5821).
     The first two output words form a 53-bit mantissa: u = (a>>5 * 2^26 + b>>6 + 0.5) / 2^53.
     """
-    idx = np.arange(start, start + count, dtype=np.uint64)
+    if indices is not None:
+        idx = np.asarray(indices, dtype=np.uint64)
+    else:
+        idx = np.arange(start, start + count, dtype=np.uint64)
     lo = (idx & _MASK32).astype(np.uint32)
     hi = (idx >> np.uint64(32)).astype(np.uint32)
     x0, x1, _, _ = philox4x32_10(lo, hi, np.uint32(stream), np.uint32(0),

@@ -95,17 +95,44 @@ def q_table(w: Workload):
     return ("table", t, w.q_a * t ** 1.5)
 
 
-def _uniform(w, stream, start, count, lo, hi):
-    return lo + (hi - lo) * uniform01(w.seed, stream, start, count)
+def _uniform(w, stream, start, count, lo, hi, idx=None):
+    return lo + (hi - lo) * uniform01(w.seed, stream, start, count, idx)
 
 
-def _loguniform(w, stream, start, count, lo, hi):
-    u = uniform01(w.seed, stream, start, count)
+def _loguniform(w, stream, start, count, lo, hi, idx=None):
+    u = uniform01(w.seed, stream, start, count, idx)
     return np.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * u)
 
 
-def _exponential(w, stream, start, count, mean):
-    return -mean * np.log(uniform01(w.seed, stream, start, count))
+def _exponential(w, stream, start, count, mean, idx=None):
+    return -mean * np.log(uniform01(w.seed, stream, start, count, idx))
+
+
+def nu0_in_chunks(w: Workload, chunk: int = 10_000_000):
+    """Yield (start, nu0) for the whole list, chunk by chunk (line centres only)."""
+    for start in range(0, w.n_lines, chunk):
+        count = min(chunk, w.n_lines - start)
+        yield start, _uniform(w, S_NU0, start, count, w.nu_lo, w.nu_hi)
+
+
+def make_lines_at(w: Workload, indices):
+    """Columns of the lines with the given generation indices (same values as make_lines)."""
+    idx = np.asarray(indices, dtype=np.uint64)
+    n = idx.size
+    wd = np.float16 if w.width_dtype == "f16" else np.float32
+    out = {
+        "nu0": _uniform(w, S_NU0, 0, n, w.nu_lo, w.nu_hi, idx),
+        "s_or_a": _loguniform(w, S_STRENGTH, 0, n, w.strength_lo, w.strength_hi, idx).astype(np.float32),
+        "e_lower": _exponential(w, S_ELOWER, 0, n, w.elower_mean, idx).astype(np.float32),
+        "gamma_ref": _uniform(w, S_GREF, 0, n, w.gamma_ref_lo, w.gamma_ref_hi, idx).astype(wd),
+        "n_t": _uniform(w, S_NT, 0, n, w.n_t_lo, w.n_t_hi, idx).astype(wd),
+        "g_up": None,
+        "convention": w.convention,
+    }
+    if w.convention == EXOMOL:
+        u = uniform01(w.seed, S_GUP, 0, n, idx)
+        out["g_up"] = (1.0 + np.floor(u * w.gup_max)).astype(np.float32)
+    return out
 
 
 def make_lines(w: Workload, start: int = 0, count: int = None):

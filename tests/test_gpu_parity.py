@@ -252,3 +252,71 @@ def test_config2_full_size_sampled_windows():
     for s in starts:
         ref = oracle.xsec_window(Ls, grid, int(s), int(s) + 96, P, T, Qt, Qr, w.mass_amu, w.cutoff)
         check_sigma(sig[0, s:s + 96], ref, M=M, label="window %d" % s)
+
+
+# ------------------------------------------------------------------ a4 for many requests (serving path)
+def _prepared_setup(n=30000, seed=91):
+    w, L = _small_lines(1, n, 295.0, 1330.0, seed)
+    lattice = (300.0, 0.01, 100001)
+    dl = to_device(L, torch)
+    return w, L, lattice, dl, rox.Prepared(dl, lattice, 25.0)
+
+
+def test_jobs_windows_match_full_xsec_and_oracle():
+    w, L, lattice, dl, prep = _prepared_setup()
+    assert prep.status()[0] == 0
+    Qr = q_pair(w, 296.0)[1]
+    reqs = [(0, 100001, 0.1, 1500.0), (12345, 777, 1e-5, 300.0), (40000, 30001, 100.0, 3000.0),
+            (99000, 1001, 3.0, 800.0), (256 * 40 + 17, 1, 0.5, 1000.0)]
+    outs, jobs = [], []
+    for first, n, P, T in reqs:
+        o = torch.full((n,), float("nan"), device="cuda")
+        outs.append(o)
+        jobs.append(rox.make_job(prep, 0, first, n, P, T, q_pair(w, T)[0], Qr, w.mass_amu, o))
+    ws = torch.empty(rox.rox_jobs_workspace_size(jobs), dtype=torch.uint8, device="cuda")
+    rox.rox_xsec_jobs([prep], jobs, ws)
+    rc, evals = rox.rox_ws_status(ws)
+    assert rc == 0
+    expect_evals = 0
+    for (first, n, P, T), o in zip(reqs, outs):
+        full, _ = _run_xsec(dl, lattice, [(P, T, q_pair(w, T)[0])], Qr, w.mass_amu, 25.0)
+        got = o.double().cpu().numpy()
+        # same lines in the same order as the full grid; only the power-of-two strength scale
+        # may differ (per-job maximum), which can change nothing but subnormal-range terms
+        check_sigma(got, full[0, first:first + n], M=float(full[0].max()), rel_tol=1e-6, label="vs full grid")
+        ref = oracle.xsec_window(L, lattice, first, first + n, P, T, q_pair(w, T)[0], Qr, w.mass_amu, 25.0)
+        check_sigma(got, ref, M=float(full[0].max()), label="job %d+%d" % (first, n))
+        jlo, jhi = oracle.window_indices(L["nu0"], *lattice, 25.0)
+        expect_evals += int(np.sum(np.maximum(np.minimum(jhi, first + n - 1) - np.maximum(jlo, first) + 1, 0)))
+    assert evals == expect_evals
+
+
+def test_jobs_alone_equals_in_mix():
+    w, L, lattice, dl, prep = _prepared_setup(20000, 93)
+    w2, L2 = _small_lines(1, 5000, 295.0, 1330.0, 95)
+    dl2 = to_device(L2, torch)
+    prep2 = rox.Prepared(dl2, lattice, 25.0)
+    Qr = q_pair(w, 296.0)[1]
+    rng = np.random.default_rng(7)
+    specs = []
+    for k in range(24):
+        n = int(rng.integers(1, 20000))
+        first = int(rng.integers(0, lattice[2] - n))
+        specs.append((int(rng.integers(0, 2)), first, n, float(10 ** rng.uniform(-5, 2)), float(rng.uniform(300, 3000))))
+    preps = [prep, prep2]
+
+    def run(subset):
+        outs, jobs = [], []
+        for li, first, n, P, T in subset:
+            o = torch.empty(n, device="cuda")
+            outs.append(o)
+            jobs.append(rox.make_job(preps[li], li, first, n, P, T, q_pair(w, T)[0], Qr, w.mass_amu, o))
+        ws = torch.empty(rox.rox_jobs_workspace_size(jobs), dtype=torch.uint8, device="cuda")
+        rox.rox_xsec_jobs(preps, jobs, ws)
+        assert rox.rox_ws_status(ws)[0] == 0
+        return [o.cpu().numpy() for o in outs]
+
+    mixed = run(specs)
+    for k, spec in enumerate(specs):
+        alone = run([spec])[0]
+        assert np.array_equal(alone, mixed[k]), k

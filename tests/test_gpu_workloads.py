@@ -1,0 +1,128 @@
+"""GPU parity on the large workloads: the 1e8-line batch over (P,T) points, the chunked
+1e9-line stream (checked on its 1e6-line subsample), and the device-side input generator.
+The oracle evaluates exact windows: a window's cross-section needs only the lines within the
+cutoff of it, regenerated on the host from their generation indices."""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import oracle
+import rox_synth as rs
+from rox_testutil import check_sigma, q_pair, to_device
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2510_20870_gb300 as rox  # noqa: E402
+from rox_synth.device import make_lines_device  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pool():
+    with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as p:
+        yield p
+
+
+def _oracle_window(args):
+    lines, grid, j0, j1, P, T, Qt, Qr, mass, cutoff = args
+    return oracle.xsec_window(lines, grid, j0, j1, P, T, Qt, Qr, mass, cutoff)
+
+
+def _window_lines(w, windows, grid, cutoff):
+    """Host-generated, nu0-sorted lines within the cutoff (+margin) of each window."""
+    lo = np.array([grid[0] + grid[1] * a - cutoff - 0.05 for a, b in windows])
+    hi = np.array([grid[0] + grid[1] * (b - 1) + cutoff + 0.05 for a, b in windows])
+    found = [[] for _ in windows]
+    for start, nu0 in rs.nu0_in_chunks(w):
+        for k in range(len(windows)):
+            found[k].append(start + np.nonzero((nu0 >= lo[k]) & (nu0 <= hi[k]))[0])
+    return [oracle.sort_lines(rs.make_lines_at(w, np.concatenate(f))) for f in found]
+
+
+def _sorted_device(w, n, start=0):
+    raw = make_lines_device(w, start, n)
+    out = {k: (torch.empty_like(v) if isinstance(v, torch.Tensor) else v) for k, v in raw.items()}
+    ws = torch.empty(rox.rox_sort_workspace_size(n), dtype=torch.uint8, device="cuda")
+    rox.rox_sort_lines(raw, out, None, ws)
+    del raw, ws
+    return out
+
+
+@pytest.mark.parametrize("cid,start,count", [(2, 0, 200_000), (2, 9_999_000, 1000), (4, 0, 100_000),
+                                             (4, 999_900_000, 100_000), (3, 77_777_777, 5000)])
+def test_device_generator_matches_host(cid, start, count):
+    w = rs.CONFIGS[cid]
+    d = make_lines_device(w, start, count)
+    h = rs.make_lines(w, start, count)
+    for k in ("nu0", "gamma_ref", "n_t", "g_up"):
+        if h[k] is not None:
+            assert np.array_equal(d[k].cpu().numpy(), h[k]), k
+    for k in ("s_or_a", "e_lower"):          # through exp/log: at most one FP32 ulp apart
+        a, b = d[k].cpu().numpy(), h[k]
+        assert np.all(np.abs(a.view(np.int32) - b.view(np.int32)) <= 1), k
+
+
+@pytest.mark.slow
+def test_batch_1e8_lines_points_in_one_launch(pool):
+    w = rs.CONFIGS[3]
+    grid = rs.grid_of(w)
+    pts_all = rs.pt_points(w)                    # 15 P x 20 T, P-major
+    pick = [(p, t) for p in (0, 7, 14) for t in (0, 10, 19)]
+    pts = [pts_all[p * 20 + t] for p, t in pick]
+    Qr = q_pair(w, 296.0)[1]
+    dl = _sorted_device(w, w.n_lines)
+    n_temps = len(set(T for _, T in pts))
+    ws = torch.empty(rox.rox_xsec_workspace_size(w.n_lines, grid, n_temps), dtype=torch.uint8, device="cuda")
+    sigma = torch.empty((len(pts), grid[2]), dtype=torch.float32, device="cuda")
+    Qts = [q_pair(w, T)[0] for _, T in pts]
+    rox.rox_xsec_batch(dl, grid, [P for P, _ in pts], [T for _, T in pts], Qts, Qr, w.mass_amu, w.cutoff, sigma, ws)
+    rc, evals = rox.rox_ws_status(ws)
+    assert rc == 0 and evals > 4e12
+    sig = sigma.cpu().numpy()
+    del dl, ws, sigma
+    windows = [(0, 48), (1_234_567, 1_234_615), (grid[2] - 48, grid[2])]
+    wl = _window_lines(w, windows, grid, w.cutoff)
+    tasks, where = [], []
+    for k, (P, T) in enumerate(pts):
+        for q, (a, b) in enumerate(windows):
+            tasks.append((wl[q], grid, a, b, P, T, Qts[k], Qr, w.mass_amu, w.cutoff))
+            where.append((k, a, b))
+    refs = pool.map(_oracle_window, tasks, chunksize=1)
+    for (k, a, b), ref in zip(where, refs):
+        check_sigma(sig[k, a:b], ref, M=float(sig[k].max()), label="P=%g T=%g [%d,%d)" % (pts[k] + (a, b)))
+
+
+@pytest.mark.slow
+def test_stream_1e9_subsample_chunked(pool):
+    w = rs.CONFIGS[4]
+    grid = rs.grid_of(w)
+    (P, T), = w.pts
+    Qt, Qr = q_pair(w, T)
+    n_sub, n_chunks = 1_000_000, 4
+    sigma = torch.zeros((1, grid[2]), dtype=torch.float32, device="cuda")
+    per = n_sub // n_chunks
+    for c in range(n_chunks):
+        dl = _sorted_device(w, per, c * per)
+        ws = torch.empty(rox.rox_xsec_workspace_size(per, grid, 1), dtype=torch.uint8, device="cuda")
+        rox.rox_xsec_batch(dl, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws, flags=rox.ROX_ACCUMULATE)
+        assert rox.rox_ws_status(ws)[0] == 0
+    chunked = sigma.double().cpu().numpy()[0]
+    # the same subsample in one call
+    dl = _sorted_device(w, n_sub)
+    ws = torch.empty(rox.rox_xsec_workspace_size(n_sub, grid, 1), dtype=torch.uint8, device="cuda")
+    one = torch.empty((1, grid[2]), dtype=torch.float32, device="cuda")
+    rox.rox_xsec(dl, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, one, ws)
+    assert rox.rox_ws_status(ws)[0] == 0
+    single = one.double().cpu().numpy()[0]
+    M = float(single.max())
+    check_sigma(chunked, single, M=M, rel_tol=2e-5, label="chunked vs single")
+    L = oracle.sort_lines(rs.make_lines(w, 0, n_sub))
+    rng = np.random.default_rng(4)
+    starts = [0, grid[2] - 64] + [int(s) for s in rng.integers(0, grid[2] - 64, 14)]
+    tasks = [(L, grid, s, s + 64, P, T, Qt, Qr, w.mass_amu, w.cutoff) for s in starts]
+    for s, ref in zip(starts, pool.map(_oracle_window, tasks, chunksize=1)):
+        check_sigma(chunked[s:s + 64], ref, M=M, label="window %d" % s)

@@ -58,3 +58,12 @@ def test_requests_fit_the_lattice():
     for r in reqs:
         assert 300.0 <= r.nu_min and r.nu_min + (r.n - 1) * 0.01 <= 30000.0 + 1e-6
         assert 1e-5 <= r.p_bar <= 1e2 and 300 <= r.t_k <= 3000 and 0 <= r.list_id < 4
+
+
+def test_lines_at_indices_match_ranges():
+    w = rs.CONFIGS[4]
+    a = rs.make_lines(w, 5000, 300)
+    idx = np.arange(5000, 5300)[::-1]
+    b = rs.make_lines_at(w, idx)
+    for k in ("nu0", "s_or_a", "e_lower", "gamma_ref", "n_t"):
+        assert np.array_equal(a[k][::-1], b[k])
