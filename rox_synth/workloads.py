@@ -65,7 +65,10 @@ CONFIGS = {
     3: Workload("batch", 100_000_000, 3, EXOMOL, 300.0, 30000.0, 1e-8, 1e2, 5000.0, 16.0,
                 300.0, 30000.0, 0.01, 25.0,
                 _pt_grid(np.logspace(-5, 2, 15), np.linspace(300.0, 3000.0, 20)), "table"),
-    4: Workload("large", 1_000_000_000, 4, HITRAN, 500.0, 10000.0, 1e-35, 1e-18, 3000.0, 18.0,
+    # E'' of the large list is not given by its description; with the HITRAN scaling at 3000 K an
+    # exponential of mean 3000 cm^-1 would push the strongest of 1e9 lines to ~1e100 cm/molecule
+    # (beyond FP32 cross-sections), so the mean is 1000 cm^-1 (strongest lines ~1e20).
+    4: Workload("large", 1_000_000_000, 4, HITRAN, 500.0, 10000.0, 1e-35, 1e-18, 1000.0, 18.0,
                 500.0, 10000.0, 0.01, 100.0, ((10.0, 3000.0),), "analytic", width_dtype="f16"),
 }
 
