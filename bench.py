@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--lines", type=int, default=None,
                     help="use only the first N lines of the workload (smaller profiling case)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving (request-latency) leg")
+    ap.add_argument("--serve-rates", default="50,100", help="Poisson request rates (req/s) of the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=6.0, help="arrival window per rate (s)")
     return ap.parse_args()
 
 
@@ -154,6 +157,48 @@ def run_reference(args):
                                  args.steps, per_step)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ serving leg (request latency)
+def serving_leg(rates, seconds):
+    """Four resident lists (1e5..1e8 lines, exomol distributions) on the 0.01 cm^-1 lattice of
+    300-30000 cm^-1; Poisson requests (list, P, T, window of 10-5000 cm^-1). Continuous batching
+    against the plain one-request-per-launch loop, same request stream."""
+    import torch
+    import paper_2510_20870_gb300 as rox
+    from paper_2510_20870_gb300 import serve
+    from rox_synth.device import make_lines_device
+
+    lattice = (300.0, 0.01, 2970001)
+    lists = []
+    for w in rs.SERVE_LISTS:
+        raw = make_lines_device(w, 0, w.n_lines)
+        out = {k: (torch.empty_like(v) if isinstance(v, torch.Tensor) else v) for k, v in raw.items()}
+        ws = torch.empty(rox.rox_sort_workspace_size(w.n_lines), dtype=torch.uint8, device="cuda")
+        rox.rox_sort_lines(raw, out, None, ws)
+        del raw, ws
+        lists.append(out)
+    w0 = rs.SERVE_LISTS[0]
+    srv = serve.Server(lists, lattice, w0.cutoff, w0.mass_amu, rs.q_table(w0), max_inflight=3, max_batch=32)
+    srv.run(serve.requests_from_stream(rs.serve_requests(200.0, 16, seed=99), lattice), realtime=False)  # warm-up
+    out = {}
+    for rate in rates:
+        reqs = serve.requests_from_stream(rs.serve_requests(rate, max(8, int(rate * seconds)), seed=5), lattice)
+        legs = {}
+        for name, opl in (("batched", False), ("one_per_launch", True)):
+            srv.evals, srv.launches = 0, 0
+            t = time.perf_counter()
+            res = srv.run(reqs, realtime=True, one_per_launch=opl)
+            wall = time.perf_counter() - t
+            st = serve.latency_stats(res)
+            st.update({"evals_per_s": srv.evals / wall, "launches": srv.launches, "wall_s": wall})
+            legs[name] = st
+        out["%g" % rate] = legs
+    del srv, lists
+    torch.cuda.empty_cache()
+    return {"workload": "4 resident lists (1e5, 1e6, 1e7, 1e8 lines), Poisson arrivals, list uniform, P log-uniform "
+                        "1e-5..1e2 bar, T uniform 300..3000 K, window 10..5000 cm^-1 at 0.01 cm^-1, cutoff 25",
+            "rates_req_per_s": out}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -327,6 +372,14 @@ def run_gpu(args):
     if csum.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / (sms * FP32_LANES_PER_SM * 2 * csum["sm_mhz"] * 1e6 / 1e12)
 
+    ws_mb = ws.numel() / 1e6
+    sigma_bytes = sigma.numel() * 4
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        del lines, raw, ws, sort_ws
+        torch.cuda.empty_cache()
+        serving = serving_leg([float(r) for r in args.serve_rates.split(",")], args.serve_seconds)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -344,11 +397,11 @@ def run_gpu(args):
                            "step": "rox_xsec on the resident nu0-sorted list (strengths, widths, windows, tile "
                                    "ranges, Voigt accumulate); the once-per-list sort is inside e2e",
                            "l2": "inputs larger than L2 (line list %.0f MB, workspace %.0f MB)" % (
-                               h2d_bytes / 1e6, ws.numel() / 1e6),
+                               h2d_bytes / 1e6, ws_mb),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof, "cpu_baseline": cpu, "serving": serving,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
-                        "d2h_bytes_per_step": sigma.numel() * 4,
+                        "d2h_bytes_per_step": sigma_bytes,
                         "ms_per_step": e2e_ms / e2e_steps if e2e_steps else None,
                         "includes": "H2D of the unsorted list, rox_sort_lines, rox_xsec, D2H of sigma"},
                 "gpu_launches": args.steps * 4,
