@@ -17,8 +17,13 @@
 // fraction gives S V = (S Y / pi)(t + 2G) / (t^2 + 4 G Y^2) with t = X^2 + Y^2 - G, i.e.
 // 4 FMAs and one reciprocal; two lines share one reciprocal (n1/d1 + n2/d2 =
 // (n1 d2 + n2 d1)/(d1 d2)), so a pair costs 12 FP32 operations and one MUFU per point.
-// Points in the slow zone go to the full FP32 Faddeeva evaluation (rox_faddeeva.cuh); the
-// choice is made per line and 32-point sub-span, so it is warp-uniform.
+// Lines are evaluated in two passes per batch. Pass 1 applies the far formula to every line
+// whose window covers the span, in pairs, with the numerator set to zero inside the line's
+// slow zone (t < t_z, one precomputed threshold: x^2 + y^2 < 22^2 or |X| below the precision
+// margin); lines cut by a window edge take the same masked formula one by one per 32-point
+// sub-span. Pass 2 evaluates exactly the complementary points (t < t_z, decided on the same
+// rounded t) with the full FP32 Faddeeva forms (rox_faddeeva.cuh), one form per 32-point
+// sub-span where possible, accumulated in warp-private shared memory.
 #include <cuda_fp16.h>
 #include "rox_internal.cuh"
 #include "rox_faddeeva.cuh"
@@ -30,8 +35,8 @@ namespace {
 
 // Per-line constants of one (P,T) point, one record per staged line:
 //   a = {k0 (exact float), f*dnu, Y^2 - G, 4 G Y^2}
-//   b = {S Y / pi, (S Y / pi) * 2G, fast flag (1: whole span inside the window and
-//        outside the slow zone), 0}
+//   b = {S Y / pi, (S Y / pi) * 2G, class bits (1: window covers the span, 2: slow zone meets
+//        the span), t_z (far formula iff t = X^2 + Y^2 - G >= t_z)}
 //   c = {jlo, jhi, zlo, zhi} (int bits; window and slow zone, inclusive grid indices)
 //   d = {1/gamma_G, y = gamma_L/gamma_G, S/(gamma_G sqrt(pi)), 0}
 // S is scaled by 2^-e (e the exponent of the largest strength at this temperature).
@@ -64,53 +69,63 @@ __device__ __forceinline__ float far_term(float X, const float4& a, const float4
   return n * rox_rcp(d);
 }
 
-// S V at one point of a sub-span that comes within |z| < 10 of a line centre: per point,
-// the 3-level fraction beyond |z| = 10, the 5-level one beyond 6, the core forms inside
-// (Weideman or Dawson by the line's y, so uniform across the warp).
-__device__ __noinline__ float zone_point(float x, float y, float pcore, const float* daw) {
-  const float s = fmaf(x, x, y * y);
-  float r;
-  if (s >= ROX_S_CF3) r = rox_re_w_cf3(x, y);
-  else if (s >= ROX_S_CF5) r = rox_re_w_cf5g(x, y);
-  else r = rox_re_w_core(daw, x, y);
-  return pcore * r;
+// far formula with the slow-zone mask of pass 1: zero where t = X^2 + Y^2 - G < t_z
+__device__ __forceinline__ float masked_far(float X, const float4& a, const float4& b) {
+  const float t = fmaf(X, X, a.z);
+  const float d = fmaf(t, t, a.w);
+  const float n = t >= b.w ? fmaf(t, b.x, b.y) : 0.0f;
+  return n * rox_rcp(d);
 }
 
-// One line whose window edge or slow zone meets the warp's span, per 32-point sub-span
-// (warp-uniform decisions): skipped if outside the window; far formula if the sub-span
-// misses the slow zone; the 3-level fraction for all 32 points if even its point nearest
-// the centre has |z| >= 10 (the fractions only get more accurate further out); per-point
-// zone_point otherwise. Sub-spans cut by the window edge are masked per point.
-__device__ __forceinline__ void slow_line(const Rec& rq, int Aw, int lane, float Jf, float dnu_f,
-                                          const float* daw, float (&acc)[ROX_K]) {
-  const float X0 = fmaf(Jf - rq.a.x, dnu_f, -rq.a.y);
-  const int jlo = __float_as_int(rq.c.x), jhi = __float_as_int(rq.c.y);
-  const int zlo = __float_as_int(rq.c.z), zhi = __float_as_int(rq.c.w);
-  const float invG = rq.d.x, y = rq.d.y, pcore = rq.d.z;
-  const float centre = rq.a.x + rq.a.y / dnu_f;     // k0 + f, within 0.25 grid steps
-  const float y2 = y * y;
+// Pass 1 for a line whose window edge falls inside the span: per 32-point sub-span, skipped if
+// outside the window, the masked far formula otherwise, masked per point where cut.
+__device__ __forceinline__ void edge_line(const float4& a, const float4& b, const float4& c, int Aw, int lane,
+                                          float Jf, float dnu_f, float (&acc)[ROX_K]) {
+  const float X0 = fmaf(Jf - a.x, dnu_f, -a.y);
+  const int jlo = __float_as_int(c.x), jhi = __float_as_int(c.y);
 #pragma unroll
   for (int m = 0; m < ROX_K; m++) {
     const int am = Aw + 32 * m, bm = am + 31;
-    if (bm < jlo || am > jhi) continue;              // sub-span outside the window
+    if (bm < jlo || am > jhi) continue;
     const int j = am + lane;
-    const bool take = (am >= jlo && bm <= jhi) || (j >= jlo && j <= jhi);
-    float v;
-    if (bm < zlo || am > zhi) {                      // far from the centre
-      v = far_term(fmaf((float)(32 * m), dnu_f, X0), rq.a, rq.b);
-    } else {
-      const float dc = (centre >= (float)am && centre <= (float)bm)
-                           ? 0.0f : fminf(fabsf((float)am - centre), fabsf((float)bm - centre));
-      const float xm = fmaxf(dc - 1.0f, 0.0f) * dnu_f * invG;
-      const float X = fmaf((float)j - rq.a.x, dnu_f, -rq.a.y);
-      const float x = fabsf(X) * invG;
-      const float sm = fmaf(xm, xm, y2);
-      const float dfar = fmaxf(fabsf((float)am - centre), fabsf((float)bm - centre)) * dnu_f * invG;
-      if (sm >= ROX_S_CF3) v = pcore * rox_re_w_cf3(x, y);
-      else if (sm >= ROX_S_CF5 && dfar < 1000.0f) v = pcore * rox_re_w_cf5g(x, y);
-      else v = zone_point(x, y, pcore, daw);
-    }
-    acc[m] += take ? v : 0.0f;
+    const float v = masked_far(fmaf((float)(32 * m), dnu_f, X0), a, b);
+    acc[m] += (j >= jlo && j <= jhi) ? v : 0.0f;
+  }
+}
+
+// Pass 2 for a line whose slow zone meets the span: exactly the points pass 1 masked out
+// (t < t_z on the same rounded t, inside the window), with the full FP32 Faddeeva forms. Per
+// 32-point sub-span one form for all points where possible: the 3-level fraction if even
+// the sub-span's point nearest the centre has |z| >= 10, the 5-level one if |z| >= 6 there
+// (both only get more accurate further out), else rox_re_w per point. Accumulated into
+// the warp's shared-memory row zacc[32 m + lane] (each lane touches only its own points).
+__device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float Jf, float dnu_f, const float* daw,
+                                          float* zacc) {
+  const float X0 = fmaf(Jf - rq.a.x, dnu_f, -rq.a.y);
+  const int jlo = __float_as_int(rq.c.x), jhi = __float_as_int(rq.c.y);
+  const int zlo = __float_as_int(rq.c.z), zhi = __float_as_int(rq.c.w);
+  const int lo = max(max(zlo, jlo), Aw), hi = min(min(zhi, jhi), Aw + ROX_SPAN - 1);
+  if (lo > hi) return;
+  const float invG = rq.d.x, y = rq.d.y, pcore = rq.d.z;
+  const float centre = rq.a.x + rq.a.y / dnu_f;     // k0 + f, within 0.25 grid steps
+  const float y2 = y * y;
+  for (int m = (lo - Aw) >> 5; m <= ((hi - Aw) >> 5); m++) {
+    const int am = Aw + 32 * m, bm = am + 31;
+    const int j = am + lane;
+    const float Xm = fmaf((float)(32 * m), dnu_f, X0);
+    const float t = fmaf(Xm, Xm, rq.a.z);
+    if (!(t < rq.b.w) || j < jlo || j > jhi) continue;
+    const float dc = (centre >= (float)am && centre <= (float)bm)
+                         ? 0.0f : fminf(fabsf((float)am - centre), fabsf((float)bm - centre));
+    const float xm = fmaxf(dc - 1.0f, 0.0f) * dnu_f * invG;
+    const float sm = fmaf(xm, xm, y2);
+    const float X = fmaf((float)j - rq.a.x, dnu_f, -rq.a.y);
+    const float x = fabsf(X) * invG;
+    float r;
+    if (sm >= ROX_S_CF3) r = rox_re_w_cf3(x, y);
+    else if (sm >= ROX_S_CF5) r = rox_re_w_cf5g(x, y);
+    else r = rox_re_w(daw, x, y);
+    zacc[32 * m + lane] += pcore * r;
   }
 }
 
@@ -118,6 +133,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
   __shared__ float4 s_geo[ROX_WARPS][2][32];
   __shared__ float s_S[ROX_WARPS][2][32];
   __shared__ Rec s_rec[ROX_WARPS][32];
+  __shared__ float s_zacc[ROX_WARPS][ROX_SPAN];
   __shared__ float s_daw[ROX_NDAW];
   __shared__ int s_status;
 
@@ -131,6 +147,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
   float4(*geo_st)[32] = s_geo[w];
   float(*S_st)[32] = s_S[w];
   Rec* rec = s_rec[w];
+  float* zacc = s_zacc[w];
   unsigned long long evals = 0;   // (line, point) pairs inside the cutoff and the job's window
 
   for (;;) {
@@ -167,7 +184,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
 
     float acc[ROX_K], tot[ROX_K], cmp[ROX_K];
 #pragma unroll
-    for (int m = 0; m < ROX_K; m++) { acc[m] = 0.f; tot[m] = 0.f; cmp[m] = 0.f; }
+    for (int m = 0; m < ROX_K; m++) { acc[m] = 0.f; tot[m] = 0.f; cmp[m] = 0.f; zacc[32 * m + lane] = 0.f; }
 
     // stage batch 0; widths go through registers one batch ahead
     float gref = 0.f, nt = 0.f;
@@ -214,14 +231,16 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         const float f = g.y / dnu_f;
         const int zlo = k0 + (int)floorf(f - hzg) - 1;
         const int zhi = k0 + (int)ceilf(f + hzg) + 1;
-        const bool fast = Aw >= jlo && Bw <= jhi && (Bw < zlo || Aw > zhi);
-        r.a = make_float4(g.x, g.y, fmaf(-0.5f, gG2, gL2), 2.0f * gG2 * gL2);
-        r.b = make_float4(pY, pY * gG2, fast ? 1.0f : 0.0f, 0.f);
+        const bool covers = Aw >= jlo && Bw <= jhi;
+        const bool zoned = !(Bw < zlo || Aw > zhi);
+        const float vg = fmaf(-0.5f, gG2, gL2);
+        r.a = make_float4(g.x, g.y, vg, 2.0f * gG2 * gL2);
+        r.b = make_float4(pY, pY * gG2, __uint_as_float((covers ? 1u : 0u) | (zoned ? 2u : 0u)), fmaf(hz, hz, vg));
         r.c = make_float4(g.z, g.w, __int_as_float(zlo), __int_as_float(zhi));
         r.d = make_float4(invG, gL * invG, Sp * invG * ROX_INV_SQRT_PI, 0.f);
       } else {   // padding record: contributes nothing
         r.a = make_float4(0.f, 0.f, 1.f, 0.f);
-        r.b = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.b = make_float4(0.f, 0.f, __uint_as_float(0u), 0.f);
         r.c = make_float4(__int_as_float(1), __int_as_float(0), __int_as_float(0), __int_as_float(0));
         r.d = make_float4(1.f, 0.f, 0.f, 0.f);
       }
@@ -230,18 +249,23 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
       nt = nt_n;
       __syncwarp();
 
-      // ---- evaluation: the batch's fast lines in pairs (sharing one reciprocal), then its
-      // slow lines one by one; both orders are fixed, so the sum is reproducible
-      unsigned fmask = __ballot_sync(0xffffffffu, lane < cnt && r.b.z != 0.f);
-      const unsigned smask = __ballot_sync(0xffffffffu, lane < cnt && r.b.z == 0.f);
-      while (fmask) {
-        const int i0 = __ffs(fmask) - 1;
-        fmask &= fmask - 1;
+      // ---- pass 1: far formula. Clean lines (window covers the span, no slow zone in it) in
+      // unmasked pairs; covering lines with a slow zone in masked pairs; window-edge lines one
+      // by one. The orders are fixed, so the sum is reproducible.
+      const unsigned cls = __float_as_uint(r.b.z);
+      const bool live = lane < cnt;
+      unsigned cmask = __ballot_sync(0xffffffffu, live && cls == 1u);
+      unsigned zmask = __ballot_sync(0xffffffffu, live && cls == 3u);
+      const unsigned emask = __ballot_sync(0xffffffffu, live && !(cls & 1u));
+      const unsigned pmask = __ballot_sync(0xffffffffu, live && (cls & 2u));
+      while (cmask) {
+        const int i0 = __ffs(cmask) - 1;
+        cmask &= cmask - 1;
         const float4 a0 = rec[i0].a, b0v = rec[i0].b;
         const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y);
-        if (fmask) {
-          const int i1 = __ffs(fmask) - 1;
-          fmask &= fmask - 1;
+        if (cmask) {
+          const int i1 = __ffs(cmask) - 1;
+          cmask &= cmask - 1;
           const float4 a1 = rec[i1].a, b1v = rec[i1].b;
           const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
 #pragma unroll
@@ -260,9 +284,41 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
           for (int m = 0; m < ROX_K; m++) acc[m] += far_term(fmaf((float)(32 * m), dnu_f, X0), a0, b0v);
         }
       }
-      for (unsigned sm = smask; sm; sm &= sm - 1) {
-        const Rec rq = rec[__ffs(sm) - 1];
-        slow_line(rq, Aw, lane, Jf, dnu_f, s_daw, acc);
+      while (zmask) {
+        const int i0 = __ffs(zmask) - 1;
+        zmask &= zmask - 1;
+        const float4 a0 = rec[i0].a, b0v = rec[i0].b;
+        const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y);
+        if (zmask) {
+          const int i1 = __ffs(zmask) - 1;
+          zmask &= zmask - 1;
+          const float4 a1 = rec[i1].a, b1v = rec[i1].b;
+          const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
+#pragma unroll
+          for (int m = 0; m < ROX_K; m++) {
+            const float x0 = fmaf((float)(32 * m), dnu_f, X0);
+            const float x1 = fmaf((float)(32 * m), dnu_f, X1);
+            const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
+            const float d0 = fmaf(t0, t0, a0.w), d1 = fmaf(t1, t1, a1.w);
+            const float n0 = t0 >= b0v.w ? fmaf(t0, b0v.x, b0v.y) : 0.0f;
+            const float n1 = t1 >= b1v.w ? fmaf(t1, b1v.x, b1v.y) : 0.0f;
+            const float dd = d0 * d1;
+            const float nn = fmaf(n1, d0, n0 * d1);
+            acc[m] = fmaf(nn, rox_rcp(dd), acc[m]);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < ROX_K; m++) acc[m] += masked_far(fmaf((float)(32 * m), dnu_f, X0), a0, b0v);
+        }
+      }
+      for (unsigned em = emask; em; em &= em - 1) {
+        const int i = __ffs(em) - 1;
+        edge_line(rec[i].a, rec[i].b, rec[i].c, Aw, lane, Jf, dnu_f, acc);
+      }
+      // ---- pass 2: the points each zoned line left out of pass 1, full Faddeeva forms
+      for (unsigned pm = pmask; pm; pm &= pm - 1) {
+        const Rec rq = rec[__ffs(pm) - 1];
+        zone_line(rq, Aw, lane, Jf, dnu_f, s_daw, zacc);
       }
       __syncwarp();
       // compensated (Kahan) accumulation of the partial sums, every 4 batches
@@ -278,6 +334,14 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
       }
     }
     cp_async_wait0();
+    // fold in the pass-2 (near-centre) sums
+#pragma unroll
+    for (int m = 0; m < ROX_K; m++) {
+      const float yk = zacc[32 * m + lane] - cmp[m];
+      const float tk = tot[m] + yk;
+      cmp[m] = (tk - tot[m]) - yk;
+      tot[m] = tk;
+    }
     // ---- write the span once (its part inside the job's window)
     float* out = J.sigma - J.first;
 #pragma unroll
