@@ -16,7 +16,7 @@ __device__ __forceinline__ double node_offset(double nu_min, double dnu, long lo
 }
 
 __global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, double nu_min,
-                          double dnu, long long n_grid, double cutoff, int32_t* jlo_out,
+                          double dnu, double inv_dnu, long long n_grid, double cutoff, int32_t* jlo_out,
                           int32_t* jhi_out, int32_t* k0_out, float* f_out, float4* geo_out,
                           unsigned long long* evals_out, int32_t* unsorted_out, int32_t unsorted_value) {
   long long stride = (long long)gridDim.x * blockDim.x;
@@ -24,9 +24,10 @@ __global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, do
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_lines; i += stride) {
     double nu0 = nu0s[i];
     if (i > 0 && nu0s[i - 1] > nu0 && unsorted_out) *unsorted_out = unsorted_value;
-    // first j with d_j >= -cutoff, last j with d_j <= cutoff (d_j non-decreasing in j)
-    double lo_c = ceil((nu0 - cutoff - nu_min) / dnu);
-    double hi_c = floor((nu0 + cutoff - nu_min) / dnu);
+    // first j with d_j >= -cutoff, last j with d_j <= cutoff (d_j non-decreasing in j): a
+    // candidate from a multiply by 1/dnu (within one index), then the exact test moves it
+    double lo_c = ceil((nu0 - cutoff - nu_min) * inv_dnu);
+    double hi_c = floor((nu0 + cutoff - nu_min) * inv_dnu);
     lo_c = fmin(fmax(lo_c, -4.0), (double)n_grid + 4.0);
     hi_c = fmin(fmax(hi_c, -4.0), (double)n_grid + 4.0);
     long long jlo = (long long)lo_c, jhi = (long long)hi_c;
@@ -37,8 +38,8 @@ __global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, do
     long long jl = jlo < 0 ? 0 : (jlo > n_grid ? n_grid : jlo);
     long long jh = jhi < -1 ? -1 : (jhi > n_grid - 1 ? n_grid - 1 : jhi);
     if (jh >= jl) ev += (unsigned long long)(jh - jl + 1);
-    // centre decomposition (nu0 - nu_min)/dnu = k0 + f
-    double u = (nu0 - nu_min) / dnu;
+    // centre decomposition (nu0 - nu_min)/dnu = k0 + f (k0 integer, f in [0, 1))
+    double u = (nu0 - nu_min) * inv_dnu;
     double k0 = floor(u);
     double f = u - k0;
     if (f >= 1.0) { k0 += 1.0; f -= 1.0; }
@@ -140,7 +141,7 @@ cudaError_t rox_launch_windows(const double* nu0, long long n_lines, const rox_g
                                int32_t* jlo, int32_t* jhi, int32_t* k0, float* f, float4* geo,
                                unsigned long long* evals, int32_t* unsorted, int32_t unsorted_value,
                                cudaStream_t s) {
-  k_windows<<<grid_for(n_lines), 256, 0, s>>>(nu0, n_lines, g->nu_min, g->dnu, g->n, cutoff, jlo, jhi, k0,
+  k_windows<<<grid_for(n_lines), 256, 0, s>>>(nu0, n_lines, g->nu_min, g->dnu, 1.0 / g->dnu, g->n, cutoff, jlo, jhi, k0,
                                                f, geo, evals, unsorted, unsorted_value);
   return cudaGetLastError();
 }
