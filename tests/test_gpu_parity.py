@@ -322,3 +322,31 @@ def test_jobs_alone_equals_in_mix():
     for k, spec in enumerate(specs):
         alone = run([spec])[0]
         assert np.array_equal(alone, mixed[k]), k
+
+
+def test_shards_on_one_gpu_reassemble_the_unsharded_result():
+    """The multi-GPU plan (no exchange): (P,T) shards and wavenumber shards computed separately
+    and concatenated give the unsharded cross-sections."""
+    from paper_2510_20870_gb300 import dist as rd
+    w, L = _small_lines(1, 12000, 4990.0, 5110.0, 51)
+    grid = (5000.0, 0.01, 10001)
+    dl = to_device(L, torch)
+    Qr = q_pair(w, 296.0)[1]
+    pts = [(P, T, q_pair(w, T)[0]) for P in (1e-3, 1.0, 30.0) for T in (500.0, 2500.0)]
+    full, _ = _run_xsec(dl, grid, pts, Qr, w.mass_amu, 25.0)
+    parts = []
+    for r in range(3):
+        sub, a = rd.point_shard(pts, 3, r)
+        parts.append(_run_xsec(dl, grid, sub, Qr, w.mass_amu, 25.0)[0])
+    assert np.array_equal(np.concatenate(parts), full)          # same strength scale per T
+    prep = rox.Prepared(dl, grid, 25.0)
+    for k, (P, T, Qt) in enumerate(pts):
+        pieces = []
+        for r in range(4):
+            first, n = rd.span_shard(grid[2], rox.ROX_SPAN, 4, r)
+            o = torch.empty(n, device="cuda")
+            job = rox.make_job(prep, 0, first, n, P, T, Qt, Qr, w.mass_amu, o)
+            ws = torch.empty(rox.rox_jobs_workspace_size([job]), dtype=torch.uint8, device="cuda")
+            rox.rox_xsec_jobs([prep], [job], ws)
+            pieces.append(o.double().cpu().numpy())
+        check_sigma(np.concatenate(pieces), full[k], rel_tol=1e-6, label="wavenumber shards")
