@@ -32,6 +32,9 @@ import numpy as np  # noqa: E402
 import rox_synth as rs  # noqa: E402
 
 FLOPS_PER_EVAL = 11.0   # far-wing pair formula: 10 FFMA + 2 FMUL per 2 evaluations (+ 1 MUFU rcp)
+# DRAM bytes per Voigt launch on the full exomol workload: ncu dram__bytes_read + write of the
+# 2e6-line case (profiles/k_voigt_exomol_2e6lines.md), scaled by evaluations (x5.0)
+VOIGT_TRAFFIC_BYTES = 2.975e8
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "Voigt line-profile evals/s"
@@ -366,7 +369,9 @@ def run_gpu(args):
     v_ms = statistics.mean(voigt_ms)
     achieved = evals * FLOPS_PER_EVAL / (v_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_voigt", "kernel_ms": v_ms,
+            "traffic": VOIGT_TRAFFIC_BYTES if (args.config == 2 and args.lines is None) else None,
+            "traffic_note": "ncu capture of the 2e6-line case scaled by evaluations", "kernel": "k_voigt",
+            "kernel_ms": v_ms,
             "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, SM_MAX_MHZ),
             "flops_per_eval": FLOPS_PER_EVAL}
     if csum.get("sm_mhz"):
