@@ -27,6 +27,8 @@ def check_sigma(gpu, ref, M=None, rel_tol=REL_TOL, label=""):
     assert worst_rel <= rel_tol, "%s: max rel err %.3e at %d (gpu %r ref %r)" % (
         label, worst_rel, int(rel.argmax()), gpu[rel.argmax()], ref[rel.argmax()])
     assert small_err <= ABS_FLOOR * M + 1e-300, "%s: abs err %.3e > %.3e" % (label, small_err, ABS_FLOOR * M)
+    print("PARITY %s: max rel err %.3e over %d points (abs err below the floor %.3e of M)" % (
+        label, worst_rel, int(big.sum()), small_err / M if M > 0 else 0.0))
     return worst_rel
 
 
