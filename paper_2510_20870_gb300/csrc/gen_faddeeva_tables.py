@@ -95,10 +95,12 @@ def main():
     out.append("#define ROX_DAW_DEG %d" % DAW_DEG)
     out.append("#define ROX_DAW_STEP %sf" % float(DAW_STEP))
     out.append("#define ROX_DAW_INV_STEP %sf" % float(1 / DAW_STEP))
-    out.append("/* d[node][n] = F^(n)(x_c)/n!, x_c = node * ROX_DAW_STEP, n = 0..ROX_DAW_DEG */")
-    out.append("ROX_TABLE float rox_daw_taylor[ROX_DAW_NODES][ROX_DAW_DEG + 1] = {")
+    out.append("/* d[node][n] = F^(n)(x_c)/n!, x_c = node * ROX_DAW_STEP, n = 0..ROX_DAW_DEG; rows padded with a")
+    out.append("   zero to an odd stride so that lanes reading consecutive nodes hit distinct shared-memory banks */")
+    out.append("#define ROX_DAW_STRIDE %d" % (DAW_DEG + 2))
+    out.append("ROX_TABLE float rox_daw_taylor[ROX_DAW_NODES][ROX_DAW_STRIDE] = {")
     for i in range(DAW_NODES):
-        d = dawson_taylor(i * DAW_STEP, DAW_DEG)
+        d = dawson_taylor(i * DAW_STEP, DAW_DEG) + [0]
         out.append("  {" + ", ".join(f32(v) for v in d) + "},")
     out.append("};")
     L, a = weideman(WEI_N)

@@ -176,7 +176,7 @@ ROX_FN float rox_re_w_weideman(float x, float y) {
 ROX_FN float rox_re_w_dawson(const float* tab, float x, float y) {
   int node = (int)rintf(x * ROX_DAW_INV_STEP);
   node = node > ROX_DAW_NODES - 1 ? ROX_DAW_NODES - 1 : (node < 0 ? 0 : node);
-  const float* d = tab + node * (ROX_DAW_DEG + 1);
+  const float* d = tab + node * ROX_DAW_STRIDE;
   float t = fmaf(-(float)node, ROX_DAW_STEP, x);
   float ar = d[ROX_DAW_DEG], ai = 0.0f;
 #pragma unroll

@@ -30,7 +30,7 @@
 
 namespace {
 
-#define ROX_NDAW (ROX_DAW_NODES * (ROX_DAW_DEG + 1))
+#define ROX_NDAW (ROX_DAW_NODES * ROX_DAW_STRIDE)
 #define ROX_INV_PI 0.318309886183790672f
 
 // Per-line constants of one (P,T) point, one record per staged line:
