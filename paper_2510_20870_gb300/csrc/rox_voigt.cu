@@ -12,18 +12,21 @@
 // the warp's shared-memory slots, and then all lanes walk the batch's lines in order. The
 // span is written once at the end, so the summation order is fixed.
 //
-// Work per (line, point) pair, in physical units X = nu_j - nu0, Y = gamma_L,
-// G = gamma_G^2 / 2: outside a per-line slow zone (x^2 + y^2 >= 22^2) the 2-level continued
-// fraction gives S V = (S Y / pi)(t + 2G) / (t^2 + 4 G Y^2) with t = X^2 + Y^2 - G, i.e.
-// 4 FMAs and one reciprocal; two lines share one reciprocal (n1/d1 + n2/d2 =
-// (n1 d2 + n2 d1)/(d1 d2)), so a pair costs 12 FP32 operations and one MUFU per point.
+// Work per (line, point) pair, in physical units X = nu_j - nu0, Y = gamma_L: outside a
+// per-line slow zone the far-zone form of rox_faddeeva.cuh (rox_re_w_far: per-line
+// coefficients alpha, beta, kappa of y = gamma_L/gamma_G), scaled by gamma_G, gives
+// S V = (S Y / pi)(t + K) / (t^2 + B) with t = X^2 + A, A = alpha gamma_G^2,
+// B = beta gamma_G^4, K = kappa gamma_G^2, i.e. 4 FMAs and one reciprocal; two lines share
+// one reciprocal (n1/d1 + n2/d2 = (n1 d2 + n2 d1)/(d1 d2)), so a pair costs 12 FP32
+// operations and one MUFU per point. The slow zone is x^2 + y^2 < 7^2 for y < 0.5 (per-line
+// Pade form) and < 22^2 otherwise (2-level continued fraction), at least the precision margin.
 // Lines are evaluated in two passes per batch. Pass 1 applies the far formula to every line
 // whose window covers the span, in pairs, with the numerator set to zero inside the line's
-// slow zone (t < t_z, one precomputed threshold: x^2 + y^2 < 22^2 or |X| below the precision
-// margin); lines cut by a window edge take the same masked formula one by one per 32-point
-// sub-span. Pass 2 evaluates exactly the complementary points (t < t_z, decided on the same
-// rounded t) with the full FP32 Faddeeva forms (rox_faddeeva.cuh), one form per 32-point
-// sub-span where possible, accumulated in warp-private shared memory.
+// slow zone (t < t_z, one precomputed threshold); lines cut by a window edge take the same
+// masked formula one by one per 32-point sub-span. Pass 2 evaluates exactly the
+// complementary points (t < t_z, decided on the same rounded t) with the full FP32 Faddeeva
+// forms (rox_faddeeva.cuh), one form per 32-point sub-span where possible, accumulated in
+// warp-private shared memory.
 #include <cuda_fp16.h>
 #include "rox_internal.cuh"
 #include "rox_faddeeva.cuh"
@@ -34,9 +37,9 @@ namespace {
 #define ROX_INV_PI 0.318309886183790672f
 
 // Per-line constants of one (P,T) point, one record per staged line:
-//   a = {k0 (exact float), f*dnu, Y^2 - G, 4 G Y^2}
-//   b = {S Y / pi, (S Y / pi) * 2G, class bits (1: window covers the span, 2: slow zone meets
-//        the span), t_z (far formula iff t = X^2 + Y^2 - G >= t_z)}
+//   a = {k0 (exact float), f*dnu, A, B}            (far form t = X^2 + A, d = t^2 + B)
+//   b = {S Y / pi, (S Y / pi) K, class bits (1: window covers the span, 2: slow zone meets
+//        the span), t_z (far formula iff t >= t_z)}
 //   c = {jlo, jhi, zlo, zhi} (int bits; window and slow zone, inclusive grid indices)
 //   d = {1/gamma_G, y = gamma_L/gamma_G, S/(gamma_G sqrt(pi)), 0}
 // S is scaled by 2^-e (e the exponent of the largest strength at this temperature).
@@ -69,11 +72,13 @@ __device__ __forceinline__ float far_term(float X, const float4& a, const float4
   return n * rox_rcp(d);
 }
 
-// far formula with the slow-zone mask of pass 1: zero where t = X^2 + Y^2 - G < t_z
+// far formula with the slow-zone mask of pass 1: zero where t < t_z (there the denominator,
+// which may vanish inside the zone, is replaced by 1)
 __device__ __forceinline__ float masked_far(float X, const float4& a, const float4& b) {
   const float t = fmaf(X, X, a.z);
-  const float d = fmaf(t, t, a.w);
-  const float n = t >= b.w ? fmaf(t, b.x, b.y) : 0.0f;
+  const bool f = t >= b.w;
+  const float d = f ? fmaf(t, t, a.w) : 1.0f;
+  const float n = f ? fmaf(t, b.x, b.y) : 0.0f;
   return n * rox_rcp(d);
 }
 
@@ -224,8 +229,10 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         const float gG2 = gG * gG, gL2 = gL * gL;
         const float pY = Sp * gL * ROX_INV_PI;
         const float invG = 1.0f / gG;
-        // slow zone: |X| < sqrt(22^2 gamma_G^2 - gamma_L^2), at least the precision margin
-        float hz = sqrtf(fmaxf(0.0f, (float)ROX_FAR_Z2 * gG2 - gL2));
+        const float yv = gL * invG;
+        const rox_far fc = rox_far_coefs(yv);      // far-zone form of this line (rox_faddeeva.cuh)
+        // slow zone: |X| < sqrt(r2 gamma_G^2 - gamma_L^2), at least the precision margin
+        float hz = sqrtf(fmaxf(0.0f, fc.r2 * gG2 - gL2));
         hz = fmaxf(hz, margin_cm);
         const float hzg = fminf(hz / dnu_f * 1.0001f, 8.0e6f);
         const float f = g.y / dnu_f;
@@ -233,11 +240,12 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         const int zhi = k0 + (int)ceilf(f + hzg) + 1;
         const bool covers = Aw >= jlo && Bw <= jhi;
         const bool zoned = !(Bw < zlo || Aw > zhi);
-        const float vg = fmaf(-0.5f, gG2, gL2);
-        r.a = make_float4(g.x, g.y, vg, 2.0f * gG2 * gL2);
-        r.b = make_float4(pY, pY * gG2, __uint_as_float((covers ? 1u : 0u) | (zoned ? 2u : 0u)), fmaf(hz, hz, vg));
+        const float vg = fc.alpha * gG2;
+        r.a = make_float4(g.x, g.y, vg, fc.beta * (gG2 * gG2));
+        r.b = make_float4(pY, pY * (fc.kappa * gG2), __uint_as_float((covers ? 1u : 0u) | (zoned ? 2u : 0u)),
+                          fmaf(hz, hz, vg));
         r.c = make_float4(g.z, g.w, __int_as_float(zlo), __int_as_float(zhi));
-        r.d = make_float4(invG, gL * invG, Sp * invG * ROX_INV_SQRT_PI, 0.f);
+        r.d = make_float4(invG, yv, Sp * invG * ROX_INV_SQRT_PI, 0.f);
       } else {   // padding record: contributes nothing
         r.a = make_float4(0.f, 0.f, 1.f, 0.f);
         r.b = make_float4(0.f, 0.f, __uint_as_float(0u), 0.f);
@@ -299,9 +307,10 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             const float x0 = fmaf((float)(32 * m), dnu_f, X0);
             const float x1 = fmaf((float)(32 * m), dnu_f, X1);
             const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
-            const float d0 = fmaf(t0, t0, a0.w), d1 = fmaf(t1, t1, a1.w);
-            const float n0 = t0 >= b0v.w ? fmaf(t0, b0v.x, b0v.y) : 0.0f;
-            const float n1 = t1 >= b1v.w ? fmaf(t1, b1v.x, b1v.y) : 0.0f;
+            const bool f0 = t0 >= b0v.w, f1 = t1 >= b1v.w;   // outside the slow zone
+            const float d0 = f0 ? fmaf(t0, t0, a0.w) : 1.0f, d1 = f1 ? fmaf(t1, t1, a1.w) : 1.0f;
+            const float n0 = f0 ? fmaf(t0, b0v.x, b0v.y) : 0.0f;
+            const float n1 = f1 ? fmaf(t1, b1v.x, b1v.y) : 0.0f;
             const float dd = d0 * d1;
             const float nn = fmaf(n1, d0, n0 * d1);
             acc[m] = fmaf(nn, rox_rcp(dd), acc[m]);

@@ -55,3 +55,60 @@ def test_special_cases(host_re_w):
     xs = np.linspace(-30, 30, 241).astype(np.float32)
     ys = np.full_like(xs, 0.37)
     assert np.array_equal(host_re_w(xs, ys), host_re_w(-xs, ys))
+
+
+@pytest.fixture(scope="module")
+def host_far():
+    import __graft_entry__
+    lib = ctypes.CDLL(__graft_entry__._build_module().build_host_lib())
+    f = lib.rox_host_re_w_far
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    r2 = lib.rox_host_far_r2
+    r2.argtypes = [ctypes.c_float]
+    r2.restype = ctypes.c_float
+
+    def call(x, y):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        out = np.empty_like(x)
+        f(x.ctypes.data, y.ctypes.data, out.ctypes.data, x.size)
+        return out
+    return call, r2
+
+
+def test_far_form_accuracy_outside_its_zone(host_far):
+    """The Voigt kernel's pair formula: the per-line Pade form (y < 0.5) from |z| = 7 outward
+    and the 2-level fraction (y >= 0.5) from |z| = 22 outward, against wofz."""
+    far, r2 = host_far
+    worst = {}
+    for y in np.concatenate([[0.0, 1e-12], np.logspace(-9, np.log10(0.4999), 120), [0.5, 0.7, 0.866, 1.0],
+                             np.logspace(0, 3, 40)]).astype(np.float32):
+        R2 = r2(float(y))
+        assert R2 == (49.0 if y < 0.5 else 484.0)
+        x0 = np.sqrt(max(0.0, R2 - float(y) ** 2))
+        x = np.concatenate([x0 + np.linspace(0, 2, 401), x0 + np.logspace(0.31, 5, 400)]).astype(np.float32)
+        x = x[x.astype(np.float64) ** 2 + float(y) ** 2 >= R2]
+        got = far(x, np.full_like(x, y)).astype(np.float64)
+        ref = wofz(x.astype(np.float64) + 1j * float(y)).real
+        m = ref > 1e-15
+        if m.any():
+            rel = np.abs(got[m] - ref[m]) / ref[m]
+            worst[float(y)] = rel.max()
+        assert np.all(np.abs(got[~m]) < 2e-15)
+    pade = max(v for k, v in worst.items() if k < 0.5)
+    cf2 = max(v for k, v in worst.items() if k >= 0.5)
+    assert pade < 5e-6, pade      # 1.8e-6 in exact arithmetic, plus FP32 rounding
+    assert cf2 < 2e-5, cf2
+
+
+def test_far_form_pade_reduces_to_series(host_far):
+    """At y -> 0 the Pade form is (y/sqrt(pi)) (u - 7/2)/(u^2 - 5u + 15/4); its expansion must
+    reproduce 1/u + 3/(2u^2) + 15/(4u^3) + 105/(8u^4) (the asymptotic series of Re w / y at y = 0)."""
+    far, _ = host_far
+    y = 1e-6
+    for u in (60.0, 200.0, 1000.0):
+        x = np.float32(np.sqrt(u))
+        got = float(far(np.array([x]), np.array([y], dtype=np.float32))[0]) * np.sqrt(np.pi) / y
+        uu = float(x) ** 2
+        series = 1 / uu + 1.5 / uu**2 + 3.75 / uu**3 + 13.125 / uu**4
+        assert abs(got - series) / series < 2e-6 + 100 / uu**4, (u, got, series)   # next term O(u^-5)
