@@ -20,7 +20,7 @@ from fractions import Fraction as Fr
 import numpy as np
 
 DAW_STEP = Fr(1, 8)      # node spacing
-DAW_NODES = 49           # x_c = 0 .. 6.0
+DAW_NODES = 59           # x_c = 0 .. 7.25
 DAW_DEG = 7
 WEI_N = 20
 

@@ -13,8 +13,11 @@
 //   s < 6^2, y >= 0.1  Weideman (1994) rational approximation, N = 20
 //   s < 6^2, y <  0.1  Re w = e^{y^2-x^2} cos(2xy) - (2/sqrt(pi)) Im F(x + iy), with
 //                      Dawson's F from its complex Taylor series around the nearest
-//                      node x_c (step 0.25). This form keeps relative accuracy in the
-//                      Gaussian tail near the real axis, where Re w is tiny next to Im w.
+//                      node x_c (step 1/8, nodes to 7.25). This form keeps relative accuracy
+//                      in the Gaussian tail near the real axis, where Re w is tiny next to
+//                      Im w.
+// The two core forms (rox_re_w_core) hold 9e-6 out to |z| = 7.1 for y < 0.5; the Voigt
+// kernel uses them directly in the |z| < 7 zone of lines with the Pade far form.
 // The continued fraction truncations miss the exponentially small e^{-z^2} part of w,
 // which can matter just outside |z| = 6 when y is essentially zero; it is added there.
 //
@@ -68,9 +71,10 @@ ROX_FN float rox_exp2(float v) {
 
 // e^{y^2 - x^2} cos(2xy): the part of w(z) = e^{-z^2} + (2i/sqrt(pi)) F(z) that the
 // asymptotic (continued fraction) forms do not contain. Used only where y < 0.1 and
-// |x| < 6, or y < 1e-6 and |x| < 10, so |2xy| < 1.2: cos by its Taylor polynomial to
-// u^10 (truncation below 2e-8), the exponential as 2^(log2(e) (y^2 - x^2)) (relative
-// error about 2e-6 at |x| = 6 from the rounded argument; results below 2^-126 flush to 0).
+// |x| < 7.1, or y < 1e-6 and |x| < 10, so |2xy| < 1.42: cos by its Taylor polynomial to
+// u^10 (truncation below 2e-7, on a term that is below e^-36 of the peak wherever |u| > 1.2),
+// the exponential as 2^(log2(e) (y^2 - x^2)) (relative error about 3e-6 at |x| = 7 from the
+// rounded argument; results below 2^-126 flush to 0).
 ROX_FN float rox_gauss_part(float x, float y) {
   const float u = 2.0f * x * y;
   const float u2 = u * u;

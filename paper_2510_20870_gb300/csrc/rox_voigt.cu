@@ -41,7 +41,8 @@ namespace {
 //   b = {S Y / pi, (S Y / pi) K, class bits (1: window covers the span, 2: slow zone meets
 //        the span), t_z (far formula iff t >= t_z)}
 //   c = {jlo, jhi, zlo, zhi} (int bits; window and slow zone, inclusive grid indices)
-//   d = {1/gamma_G, y = gamma_L/gamma_G, S/(gamma_G sqrt(pi)), 0}
+//   d = {1/gamma_G, y = gamma_L/gamma_G, S/(gamma_G sqrt(pi)), 1 if the slow zone is |z| < 7
+//        (per-line Pade far form, not widened by the precision margin), else 0}
 // S is scaled by 2^-e (e the exponent of the largest strength at this temperature).
 struct __align__(16) Rec {
   float4 a, b, c, d;
@@ -99,11 +100,13 @@ __device__ __forceinline__ void edge_line(const float4& a, const float4& b, cons
 }
 
 // Pass 2 for a line whose slow zone meets the span: exactly the points pass 1 masked out
-// (t < t_z on the same rounded t, inside the window), with the full FP32 Faddeeva forms. Per
-// 32-point sub-span one form for all points where possible: the 3-level fraction if even
-// the sub-span's point nearest the centre has |z| >= 10, the 5-level one if |z| >= 6 there
-// (both only get more accurate further out), else rox_re_w per point. Accumulated into
-// the warp's shared-memory row zacc[32 m + lane] (each lane touches only its own points).
+// (t < t_z on the same rounded t, inside the window), with the full FP32 Faddeeva forms.
+// A zone of |z| < 7 takes the core forms at every point (rox_re_w_core holds 9e-6 out to
+// |z| = 7.1). Otherwise, per 32-point sub-span, one form for all points where possible: the
+// 3-level fraction if even the sub-span's point nearest the centre has |z| >= 10, the
+// 5-level one if |z| >= 6 there (both only get more accurate further out), else rox_re_w
+// per point. Accumulated into the warp's shared-memory row zacc[32 m + lane] (each lane
+// touches only its own points).
 __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float Jf, float dnu_f, const float* daw,
                                           float* zacc) {
   const float X0 = fmaf(Jf - rq.a.x, dnu_f, -rq.a.y);
@@ -112,6 +115,17 @@ __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float
   const int lo = max(max(zlo, jlo), Aw), hi = min(min(zhi, jhi), Aw + ROX_SPAN - 1);
   if (lo > hi) return;
   const float invG = rq.d.x, y = rq.d.y, pcore = rq.d.z;
+  if (rq.d.w != 0.0f) {
+    for (int m = (lo - Aw) >> 5; m <= ((hi - Aw) >> 5); m++) {
+      const int j = Aw + 32 * m + lane;
+      const float Xm = fmaf((float)(32 * m), dnu_f, X0);
+      const float t = fmaf(Xm, Xm, rq.a.z);
+      if (!(t < rq.b.w) || j < jlo || j > jhi) continue;
+      const float X = fmaf((float)j - rq.a.x, dnu_f, -rq.a.y);
+      zacc[32 * m + lane] += pcore * rox_re_w_core(daw, fabsf(X) * invG, y);
+    }
+    return;
+  }
   const float centre = rq.a.x + rq.a.y / dnu_f;     // k0 + f, within 0.25 grid steps
   const float y2 = y * y;
   for (int m = (lo - Aw) >> 5; m <= ((hi - Aw) >> 5); m++) {
@@ -233,6 +247,8 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         const rox_far fc = rox_far_coefs(yv);      // far-zone form of this line (rox_faddeeva.cuh)
         // slow zone: |X| < sqrt(r2 gamma_G^2 - gamma_L^2), at least the precision margin
         float hz = sqrtf(fmaxf(0.0f, fc.r2 * gG2 - gL2));
+        // zone |z| < 7 not widened by the margin: the core forms cover all of it
+        const bool core_only = fc.r2 == ROX_S_PADE && hz >= margin_cm;
         hz = fmaxf(hz, margin_cm);
         const float hzg = fminf(hz / dnu_f * 1.0001f, 8.0e6f);
         const float f = g.y / dnu_f;
@@ -245,7 +261,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         r.b = make_float4(pY, pY * (fc.kappa * gG2), __uint_as_float((covers ? 1u : 0u) | (zoned ? 2u : 0u)),
                           fmaf(hz, hz, vg));
         r.c = make_float4(g.z, g.w, __int_as_float(zlo), __int_as_float(zhi));
-        r.d = make_float4(invG, yv, Sp * invG * ROX_INV_SQRT_PI, 0.f);
+        r.d = make_float4(invG, yv, Sp * invG * ROX_INV_SQRT_PI, core_only ? 1.0f : 0.0f);
       } else {   // padding record: contributes nothing
         r.a = make_float4(0.f, 0.f, 1.f, 0.f);
         r.b = make_float4(0.f, 0.f, __uint_as_float(0u), 0.f);

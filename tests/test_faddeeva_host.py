@@ -112,3 +112,23 @@ def test_far_form_pade_reduces_to_series(host_far):
         uu = float(x) ** 2
         series = 1 / uu + 1.5 / uu**2 + 3.75 / uu**3 + 13.125 / uu**4
         assert abs(got - series) / series < 2e-6 + 100 / uu**4, (u, got, series)   # next term O(u^-5)
+
+
+def test_core_forms_to_radius_7():
+    """rox_re_w_core (Dawson-Taylor for y < 0.1, Weideman above) stands alone in the Voigt
+    kernel's |z| < 7 zone of lines with the Pade far form (y < 0.5): it must hold out to
+    |z| = 7.1 there."""
+    import __graft_entry__
+    lib = ctypes.CDLL(__graft_entry__._build_module().build_host_lib())
+    f = lib.rox_host_re_w_core
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    worst = 0.0
+    for y in np.concatenate([[0.0, 1e-9], np.logspace(-7, np.log10(0.4999), 150)]):
+        x = np.linspace(0, np.sqrt(max(0.0, 7.1 ** 2 - y * y)), 1500).astype(np.float32)
+        yy = np.full_like(x, np.float32(y))
+        out = np.empty_like(x)
+        f(x.ctypes.data, yy.ctypes.data, out.ctypes.data, x.size)
+        ref = wofz(x.astype(np.float64) + 1j * float(yy[0])).real
+        m = ref > 1e-15
+        worst = max(worst, float((np.abs(out.astype(np.float64) - ref)[m] / ref[m]).max()))
+    assert worst < 1.5e-5, worst
