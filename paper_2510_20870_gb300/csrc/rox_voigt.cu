@@ -23,7 +23,7 @@
 // Lines are evaluated in two passes per batch. Pass 1 applies the far formula to every line
 // whose window covers the span, in pairs, with the numerator set to zero inside the line's
 // slow zone (t < t_z, one precomputed threshold); lines cut by a window edge take the same
-// masked formula one by one per 32-point sub-span. Pass 2 evaluates exactly the
+// masked formula in pairs too, with per-point window masks. Pass 2 evaluates exactly the
 // complementary points (t < t_z, decided on the same rounded t) with the full FP32 Faddeeva
 // forms (rox_faddeeva.cuh), one form per 32-point sub-span where possible, accumulated in
 // warp-private shared memory.
@@ -96,6 +96,33 @@ __device__ __forceinline__ void edge_line(const float4& a, const float4& b, cons
     const int j = am + lane;
     const float v = masked_far(fmaf((float)(32 * m), dnu_f, X0), a, b);
     acc[m] += (j >= jlo && j <= jhi) ? v : 0.0f;
+  }
+}
+
+// Pass 1 for two lines cut by window edges, sharing one reciprocal as the covering lines do.
+// The sub-spans outside both windows are skipped (warp-uniform test); elsewhere each point
+// takes line i iff it lies in the window, m in [ceil((jlo-Aw-lane)/32), floor((jhi-Aw-lane)/32)]
+// (the exact integer window), and outside the slow zone. Lines arrive sorted by nu0, so
+// paired edge lines have their edges in the same or a neighbouring sub-span.
+__device__ __forceinline__ void edge_pair(const Rec& r0, const Rec& r1, int Aw, int lane, float Jf, float dnu_f,
+                                          float (&acc)[ROX_K]) {
+  const float4 a0 = r0.a, b0 = r0.b, a1 = r1.a, b1 = r1.b;
+  const int lo0 = __float_as_int(r0.c.x) - Aw, hi0 = __float_as_int(r0.c.y) - Aw;
+  const int lo1 = __float_as_int(r1.c.x) - Aw, hi1 = __float_as_int(r1.c.y) - Aw;
+  const int mf = max(0, min(lo0, lo1) >> 5), ml = min(ROX_K - 1, max(hi0, hi1) >> 5);
+  const int mlo0 = (lo0 - lane + 31) >> 5, mhi0 = (hi0 - lane) >> 5;   // this lane's window, in m
+  const int mlo1 = (lo1 - lane + 31) >> 5, mhi1 = (hi1 - lane) >> 5;
+  const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y), X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
+#pragma unroll
+  for (int m = 0; m < ROX_K; m++) {
+    if (m < mf || m > ml) continue;
+    const float x0 = fmaf((float)(32 * m), dnu_f, X0), x1 = fmaf((float)(32 * m), dnu_f, X1);
+    const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
+    const bool f0 = t0 >= b0.w && m >= mlo0 && m <= mhi0;
+    const bool f1 = t1 >= b1.w && m >= mlo1 && m <= mhi1;
+    const float d0 = f0 ? fmaf(t0, t0, a0.w) : 1.0f, d1 = f1 ? fmaf(t1, t1, a1.w) : 1.0f;
+    const float n0 = f0 ? fmaf(t0, b0.x, b0.y) : 0.0f, n1 = f1 ? fmaf(t1, b1.x, b1.y) : 0.0f;
+    acc[m] = fmaf(fmaf(n1, d0, n0 * d1), rox_rcp(d0 * d1), acc[m]);
   }
 }
 
@@ -274,8 +301,8 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
       __syncwarp();
 
       // ---- pass 1: far formula. Clean lines (window covers the span, no slow zone in it) in
-      // unmasked pairs; covering lines with a slow zone in masked pairs; window-edge lines one
-      // by one. The orders are fixed, so the sum is reproducible.
+      // unmasked pairs; covering lines with a slow zone in masked pairs; window-edge lines in
+      // pairs with window masks. The orders are fixed, so the sum is reproducible.
       const unsigned cls = __float_as_uint(r.b.z);
       const bool live = lane < cnt;
       unsigned cmask = __ballot_sync(0xffffffffu, live && cls == 1u);
@@ -336,9 +363,16 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
           for (int m = 0; m < ROX_K; m++) acc[m] += masked_far(fmaf((float)(32 * m), dnu_f, X0), a0, b0v);
         }
       }
-      for (unsigned em = emask; em; em &= em - 1) {
-        const int i = __ffs(em) - 1;
-        edge_line(rec[i].a, rec[i].b, rec[i].c, Aw, lane, Jf, dnu_f, acc);
+      for (unsigned em = emask; em;) {
+        const int i0 = __ffs(em) - 1;
+        em &= em - 1;
+        if (!em) {
+          edge_line(rec[i0].a, rec[i0].b, rec[i0].c, Aw, lane, Jf, dnu_f, acc);
+          break;
+        }
+        const int i1 = __ffs(em) - 1;
+        em &= em - 1;
+        edge_pair(rec[i0], rec[i1], Aw, lane, Jf, dnu_f, acc);
       }
       // ---- pass 2: the points each zoned line left out of pass 1, full Faddeeva forms
       for (unsigned pm = pmask; pm; pm &= pm - 1) {
