@@ -17,13 +17,13 @@
 //                      in the Gaussian tail near the real axis, where Re w is tiny next to
 //                      Im w.
 // The two core forms (rox_re_w_core) hold 9e-6 out to |z| = 7.1 for y < 0.5; the Voigt
-// kernel uses them directly in the |z| < 7 zone of lines with the Pade far form.
+// kernel uses them directly in the |z| < 6.5 zone of lines with the Pade far form.
 // The continued fraction truncations miss the exponentially small e^{-z^2} part of w,
 // which can matter just outside |z| = 6 when y is essentially zero; it is added there.
 //
 // The Voigt kernel's far zone (rox_re_w_far) uses one rational form in u = x^2 per line,
 // whose coefficients depend on y only: for y < 0.5 a [1/2] Pade approximant in 1/u of the
-// large-|x| expansion of Re w at fixed y, valid for s >= 7^2; otherwise the 2-level fraction,
+// large-|x| expansion of Re w at fixed y, valid for s >= 6.5^2; otherwise the 2-level fraction,
 // valid for s >= 22^2.
 #pragma once
 #include <math.h>
@@ -46,7 +46,7 @@
 #define ROX_S_CF3 100.0f     // 10^2
 #define ROX_S_CF5 36.0f      // 6^2
 #define ROX_Y_WEIDEMAN 0.1f
-#define ROX_S_PADE 49.0f     // 7^2: far-zone boundary of the per-line Pade form
+#define ROX_S_PADE 42.25f    // 6.5^2: far-zone boundary of the per-line Pade form
 #define ROX_Y_PADE 0.5f      // the Pade form is used for y below this
 
 ROX_FN float rox_rcp(float v) {
@@ -103,9 +103,10 @@ ROX_FN float rox_re_w_cf2(float x, float y) {
 // sqrt(pi)/y in powers of 1/u at fixed v = y^2, obtained from the asymptotic series
 // w ~ (i/sqrt(pi)) sum_n (2n-1)!!/2^n z^-(2n+1):
 //   1/u + (3/2 - v)/u^2 + (v^2 - 5v + 15/4)/u^3 + (-v^3 + 21v^2/2 - 105v/4 + 105/8)/u^4.
-// Max relative error against wofz 1.8e-6 for s >= 49, y < 0.5 (the Gaussian part e^{-x^2}
-// is below 5e-22 there). The denominator has real roots at u < 4.1 (|x| < 2.03), inside
-// |z| < 7, where the form is never used. For y >= 0.5 (the approximant has a pole at
+// Max relative error against wofz 3.4e-6 for s >= 6.5^2, 1e-9 <= y < 0.5. The form lacks the
+// Gaussian part e^{-x^2} (below 4.5e-19 of the line peak there), which is why the relative
+// bound needs y >= 1e-9; for smaller y the absolute error stays below 4.5e-19 of the peak. The denominator has real roots at
+// u < 4.1 (|x| < 2.03), inside |z| < 6.5, where the form is never used. For y >= 0.5 (the approximant has a pole at
 // v = 3/4): the 2-level continued fraction, alpha = v - 1/2, beta = 2v, kappa = 1, s >= 22^2.
 struct rox_far {
   float alpha, beta, kappa, r2;

@@ -24,10 +24,10 @@
 #define ROX_TILE ROX_SPAN               // grid points per work item (per-item line ranges)
 
 // The far formula (rox_re_w_far in physical units) is used only outside each line's slow
-// zone, x^2 + y^2 >= 7^2 or 22^2 depending on the line's y. Its per-point offset is X_m = X_0 + 32 m dnu with X_0 the offset at
-// the thread's first point, so X_m carries a rounding error of 6e-8 (|X_m| + span); the
-// slow zone around each line is therefore at least ROX_FAST_MARGIN * span wide, which
-// keeps that error below 2e-6 relative.
+// zone, x^2 + y^2 >= 6.5^2 or 22^2 depending on the line's y. Its per-point offset is
+// X_m = X_0 + 32 m dnu with X_0 the offset at the thread's first point, so X_m carries a
+// rounding error of 6e-8 (|X_m| + span); the slow zone around each line is therefore at
+// least ROX_FAST_MARGIN * span wide, which keeps that error below 2e-6 relative.
 #define ROX_FAST_MARGIN 0.032
 
 // Workspace header at the start of every xsec / prepared-list workspace.

@@ -18,7 +18,7 @@
 // S V = (S Y / pi)(t + K) / (t^2 + B) with t = X^2 + A, A = alpha gamma_G^2,
 // B = beta gamma_G^4, K = kappa gamma_G^2, i.e. 4 FMAs and one reciprocal; two lines share
 // one reciprocal (n1/d1 + n2/d2 = (n1 d2 + n2 d1)/(d1 d2)), so a pair costs 12 FP32
-// operations and one MUFU per point. The slow zone is x^2 + y^2 < 7^2 for y < 0.5 (per-line
+// operations and one MUFU per point. The slow zone is x^2 + y^2 < 6.5^2 for y < 0.5 (per-line
 // Pade form) and < 22^2 otherwise (2-level continued fraction), at least the precision margin.
 // Lines are evaluated in two passes per batch. Pass 1 applies the far formula to every line
 // whose window covers the span, in pairs, with the numerator set to zero inside the line's
@@ -41,7 +41,7 @@ namespace {
 //   b = {S Y / pi, (S Y / pi) K, class bits (1: window covers the span, 2: slow zone meets
 //        the span), t_z (far formula iff t >= t_z)}
 //   c = {jlo, jhi, zlo, zhi} (int bits; window and slow zone, inclusive grid indices)
-//   d = {1/gamma_G, y = gamma_L/gamma_G, S/(gamma_G sqrt(pi)), 1 if the slow zone is |z| < 7
+//   d = {1/gamma_G, y = gamma_L/gamma_G, S/(gamma_G sqrt(pi)), 1 if the slow zone is |z| < 6.5
 //        (per-line Pade far form, not widened by the precision margin), else 0}
 // S is scaled by 2^-e (e the exponent of the largest strength at this temperature).
 struct __align__(16) Rec {
@@ -112,12 +112,22 @@ __device__ __forceinline__ void edge_pair(const Rec& r0, const Rec& r1, int Aw, 
   const int mf = max(0, min(lo0, lo1) >> 5), ml = min(ROX_K - 1, max(hi0, hi1) >> 5);
   const int mlo0 = (lo0 - lane + 31) >> 5, mhi0 = (hi0 - lane) >> 5;   // this lane's window, in m
   const int mlo1 = (lo1 - lane + 31) >> 5, mhi1 = (hi1 - lane) >> 5;
+  // sub-spans inside both windows, when neither line's slow zone meets the span: no masks
+  const bool nozone = !((__float_as_uint(b0.z) | __float_as_uint(b1.z)) & 2u);
+  const int cf = nozone ? max((lo0 + 31) >> 5, (lo1 + 31) >> 5) : ROX_K;
+  const int cl = min((hi0 - 31) >> 5, (hi1 - 31) >> 5);
   const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y), X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
 #pragma unroll
   for (int m = 0; m < ROX_K; m++) {
     if (m < mf || m > ml) continue;
     const float x0 = fmaf((float)(32 * m), dnu_f, X0), x1 = fmaf((float)(32 * m), dnu_f, X1);
     const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
+    if (m >= cf && m <= cl) {
+      const float d0 = fmaf(t0, t0, a0.w), d1 = fmaf(t1, t1, a1.w);
+      const float n0 = fmaf(t0, b0.x, b0.y), n1 = fmaf(t1, b1.x, b1.y);
+      acc[m] = fmaf(fmaf(n1, d0, n0 * d1), rox_rcp(d0 * d1), acc[m]);
+      continue;
+    }
     const bool f0 = t0 >= b0.w && m >= mlo0 && m <= mhi0;
     const bool f1 = t1 >= b1.w && m >= mlo1 && m <= mhi1;
     const float d0 = f0 ? fmaf(t0, t0, a0.w) : 1.0f, d1 = f1 ? fmaf(t1, t1, a1.w) : 1.0f;
@@ -128,7 +138,7 @@ __device__ __forceinline__ void edge_pair(const Rec& r0, const Rec& r1, int Aw, 
 
 // Pass 2 for a line whose slow zone meets the span: exactly the points pass 1 masked out
 // (t < t_z on the same rounded t, inside the window), with the full FP32 Faddeeva forms.
-// A zone of |z| < 7 takes the core forms at every point (rox_re_w_core holds 9e-6 out to
+// A zone of |z| < 6.5 takes the core forms at every point (rox_re_w_core holds 9e-6 out to
 // |z| = 7.1). Otherwise, per 32-point sub-span, one form for all points where possible: the
 // 3-level fraction if even the sub-span's point nearest the centre has |z| >= 10, the
 // 5-level one if |z| >= 6 there (both only get more accurate further out), else rox_re_w
@@ -274,7 +284,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         const rox_far fc = rox_far_coefs(yv);      // far-zone form of this line (rox_faddeeva.cuh)
         // slow zone: |X| < sqrt(r2 gamma_G^2 - gamma_L^2), at least the precision margin
         float hz = sqrtf(fmaxf(0.0f, fc.r2 * gG2 - gL2));
-        // zone |z| < 7 not widened by the margin: the core forms cover all of it
+        // zone |z| < 6.5 not widened by the margin: the core forms cover all of it
         const bool core_only = fc.r2 == ROX_S_PADE && hz >= margin_cm;
         hz = fmaxf(hz, margin_cm);
         const float hzg = fminf(hz / dnu_f * 1.0001f, 8.0e6f);

@@ -77,19 +77,24 @@ def host_far():
 
 
 def test_far_form_accuracy_outside_its_zone(host_far):
-    """The Voigt kernel's pair formula: the per-line Pade form (y < 0.5) from |z| = 7 outward
+    """The Voigt kernel's pair formula: the per-line Pade form (y < 0.5) from |z| = 6.5 outward
     and the 2-level fraction (y >= 0.5) from |z| = 22 outward, against wofz."""
     far, r2 = host_far
     worst = {}
     for y in np.concatenate([[0.0, 1e-12], np.logspace(-9, np.log10(0.4999), 120), [0.5, 0.7, 0.866, 1.0],
                              np.logspace(0, 3, 40)]).astype(np.float32):
         R2 = r2(float(y))
-        assert R2 == (49.0 if y < 0.5 else 484.0)
+        assert R2 == (42.25 if y < 0.5 else 484.0)
         x0 = np.sqrt(max(0.0, R2 - float(y) ** 2))
         x = np.concatenate([x0 + np.linspace(0, 2, 401), x0 + np.logspace(0.31, 5, 400)]).astype(np.float32)
         x = x[x.astype(np.float64) ** 2 + float(y) ** 2 >= R2]
         got = far(x, np.full_like(x, y)).astype(np.float64)
         ref = wofz(x.astype(np.float64) + 1j * float(y)).real
+        if R2 < 484.0 and y < 1e-9:
+            # the form omits e^{-x^2} <= e^{-42.25} = 4.5e-19 (of the line peak, Re w(0, y) ~ 1);
+            # below y = 1e-9 that part is no longer small next to the Lorentz wing itself
+            assert np.all(np.abs(got - ref) < 5e-19)
+            continue
         m = ref > 1e-15
         if m.any():
             rel = np.abs(got[m] - ref[m]) / ref[m]
@@ -97,7 +102,7 @@ def test_far_form_accuracy_outside_its_zone(host_far):
         assert np.all(np.abs(got[~m]) < 2e-15)
     pade = max(v for k, v in worst.items() if k < 0.5)
     cf2 = max(v for k, v in worst.items() if k >= 0.5)
-    assert pade < 5e-6, pade      # 1.8e-6 in exact arithmetic, plus FP32 rounding
+    assert pade < 6e-6, pade      # 3.4e-6 in exact arithmetic, plus FP32 rounding
     assert cf2 < 2e-5, cf2
 
 
@@ -116,7 +121,7 @@ def test_far_form_pade_reduces_to_series(host_far):
 
 def test_core_forms_to_radius_7():
     """rox_re_w_core (Dawson-Taylor for y < 0.1, Weideman above) stands alone in the Voigt
-    kernel's |z| < 7 zone of lines with the Pade far form (y < 0.5): it must hold out to
+    kernel's |z| < 6.5 zone of lines with the Pade far form (y < 0.5): it must hold out to
     |z| = 7.1 there."""
     import __graft_entry__
     lib = ctypes.CDLL(__graft_entry__._build_module().build_host_lib())
