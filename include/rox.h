@@ -240,7 +240,7 @@ int rox_set_profile_events(void* start, void* stop);
  * device memory, a plugin that is not allowed to call cudaMalloc, or an interface that
  * has no way to pass a workspace through. The paper has no counterpart; this is a
  * packaging convenience of this library.
- * The scratch lives in one fixed array inside the library (8 MiB of device memory held on
+ * The scratch lives in one fixed array inside the library (16 MiB of device memory held on
  * every GPU that loads the library, until the process exits), so sizes are limited to
  * lines->n <= ROX_STATIC_MAX_LINES and grid->n <= ROX_STATIC_MAX_GRID; larger problems
  * return ROX_ERANGE (use rox_xsec with a workspace). Arguments and results are those of

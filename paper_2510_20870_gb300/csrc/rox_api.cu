@@ -106,6 +106,9 @@ struct WsLayout {
   long long* thi;
   double* S_T;
   float* S32;
+  float* tail_part;
+  int32_t* tail_cnt;
+  long long tail_cap;
   size_t bytes;
 };
 
@@ -126,6 +129,10 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps) {
   off += rox_align256((size_t)n_temps * (size_t)(n_lines > 0 ? n_lines : 1) * 8);
   w.S32 = (float*)(base + off);
   off += rox_align256((size_t)n_temps * (size_t)(n_lines > 0 ? n_lines : 1) * 4);
+  w.tail_cap = nt < ROX_TAIL_ITEMS_MAX ? nt : ROX_TAIL_ITEMS_MAX;
+  w.tail_part = (float*)(base + off);
+  w.tail_cnt = (int32_t*)(base + off + rox_align256((size_t)w.tail_cap * ROX_PARTS * ROX_SPAN * sizeof(float)));
+  off += rox_tail_bytes(w.tail_cap);
   w.bytes = off;
   return w;
 }
@@ -151,11 +158,14 @@ int voigt_grid(int* out) {
 }
 
 // Voigt launches over the jobs, at most ROX_MAX_JOBS per launch; the work counter is reset
-// before each launch (the evaluation count keeps adding up).
+// before each launch (the evaluation count keeps adding up). The last items of each launch,
+// up to tail_cap and half a round of the launch's warps, are split into their parts.
 int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* jobs, int n_jobs, RoxWsHeader* hdr,
-                      int nblocks, cudaStream_t s) {
+                      float* tail_part, int32_t* tail_cnt, long long tail_cap, int nblocks, cudaStream_t s) {
   static thread_local RoxVoigtArgs A;   // ~30 KB of per-job parameters, passed by value
   A.hdr = hdr;
+  A.tail_part = tail_part;
+  A.tail_cnt = tail_cnt;
   for (int l = 0; l < n_lists; l++) A.list[l] = lists[l];
   for (int j0 = 0; j0 < n_jobs; j0 += ROX_MAX_JOBS) {
     const int nj = (n_jobs - j0) < ROX_MAX_JOBS ? (n_jobs - j0) : ROX_MAX_JOBS;
@@ -165,13 +175,20 @@ int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* job
       items += A.job[k].n_spans;
       A.item_end[k] = items;
     }
+    const int blocks = items < nblocks ? items : nblocks;
+    long long split = (long long)blocks * ROX_WARPS / 2;
+    if (split > items / 2) split = items / 2;
+    if (split > tail_cap) split = tail_cap;
     A.n_jobs = nj;
     A.n_items = items;
+    A.n_whole = items - (int)split;
+    A.n_queue = A.n_whole + (int)split * ROX_PARTS;
     int rc;
     if ((rc = cuda_check(cudaMemsetAsync(&hdr->work_counter, 0, sizeof(int32_t), s), "memset"))) return rc;
+    if (split > 0 && (rc = cuda_check(cudaMemsetAsync(tail_cnt, 0, (size_t)split * 4, s), "memset"))) return rc;
     if (j0 == 0 && g_prof_start && (rc = cuda_check(cudaEventRecord(g_prof_start, s), "cudaEventRecord"))) return rc;
     if (items == 0) continue;
-    if ((rc = cuda_check(rox_launch_voigt(A, items < nblocks ? items : nblocks, s), "voigt kernel"))) return rc;
+    if ((rc = cuda_check(rox_launch_voigt(A, blocks, s), "voigt kernel"))) return rc;
   }
   if (g_prof_stop) return cuda_check(cudaEventRecord(g_prof_stop, s), "cudaEventRecord");
   return ROX_OK;
@@ -351,7 +368,8 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
     J.flags = flags;
     J.pad = 0;
   }
-  if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, nblocks, s))) return rc;
+  if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, w.tail_part, w.tail_cnt, w.tail_cap, nblocks, s)))
+    return rc;
   return ok();
 }
 
@@ -425,22 +443,37 @@ int rox_prepare(const rox_lines* lines, const rox_grid* lattice, double cutoff, 
 }
 
 namespace {
-size_t jobs_layout(const rox_job* jobs, int n_jobs, void* ws, double** S64, float** S32) {
+struct JobsTail {
+  float* part;
+  int32_t* cnt;
+  long long cap;
+};
+size_t jobs_layout(const rox_job* jobs, int n_jobs, void* ws, double** S64, float** S32, JobsTail* tail) {
   size_t off = ROX_WS_HEADER_BYTES;
+  long long spans = 0;
   for (int k = 0; k < n_jobs; k++) {
     const size_t c = (size_t)(jobs[k].line_count > 0 ? jobs[k].line_count : 1);
     if (S64) S64[k] = (double*)((char*)ws + off);
     off += rox_align256(c * 8);
     if (S32) S32[k] = (float*)((char*)ws + off);
     off += rox_align256(c * 4);
+    if (jobs[k].n > 0 && jobs[k].first >= 0)
+      spans += (jobs[k].first + jobs[k].n - 1) / ROX_SPAN - jobs[k].first / ROX_SPAN + 1;
   }
+  const long long cap = spans < ROX_TAIL_ITEMS_MAX ? spans : ROX_TAIL_ITEMS_MAX;
+  if (tail) {
+    tail->cap = cap;
+    tail->part = (float*)((char*)ws + off);
+    tail->cnt = (int32_t*)((char*)ws + off + rox_align256((size_t)cap * ROX_PARTS * ROX_SPAN * sizeof(float)));
+  }
+  off += rox_tail_bytes(cap);
   return off;
 }
 }  // namespace
 
 size_t rox_jobs_workspace_size(const rox_job* jobs, int n_jobs) {
   if (!jobs || n_jobs <= 0) return 0;
-  return jobs_layout(jobs, n_jobs, nullptr, nullptr, nullptr);
+  return jobs_layout(jobs, n_jobs, nullptr, nullptr, nullptr, nullptr);
 }
 
 int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, int n_jobs, void* ws, size_t ws_bytes,
@@ -468,7 +501,7 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     if (!j.sigma_out) return fail(ROX_EINVAL, "job %d: sigma_out is NULL", k);
   }
   if (!ws || ((uintptr_t)ws & 255)) return fail(ROX_EINVAL, "workspace NULL or not 256-byte aligned");
-  const size_t need = jobs_layout(jobs, n_jobs, nullptr, nullptr, nullptr);
+  const size_t need = jobs_layout(jobs, n_jobs, nullptr, nullptr, nullptr, nullptr);
   if (ws_bytes < need) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
   int nblocks = 0;
   if ((rc = voigt_grid(&nblocks))) return rc;
@@ -476,7 +509,8 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
   RoxWsHeader* hdr = (RoxWsHeader*)ws;
   std::vector<double*> S64(n_jobs);
   std::vector<float*> S32(n_jobs);
-  jobs_layout(jobs, n_jobs, ws, S64.data(), S32.data());
+  JobsTail tail;
+  jobs_layout(jobs, n_jobs, ws, S64.data(), S32.data(), &tail);
   if ((rc = cuda_check(cudaMemsetAsync(hdr, 0, sizeof(RoxWsHeader), s), "memset"))) return rc;
 
   // strengths of every job's line range at its temperature
@@ -545,7 +579,8 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     d.flags = j.flags;
     d.pad = 0;
   }
-  if ((rc = launch_voigt_jobs(L, n_lists, J.data(), n_jobs, hdr, nblocks, s))) return rc;
+  if ((rc = launch_voigt_jobs(L, n_lists, J.data(), n_jobs, hdr, tail.part, tail.cnt, tail.cap, nblocks, s)))
+    return rc;
   return ok();
 }
 

@@ -79,10 +79,23 @@ struct RoxJobDev {
   uint32_t pad;
 };
 
+// Every span's lines are summed as ROX_PARTS consecutive parts (batch-aligned), each from
+// zero, and the part sums are added in part order. A work item is normally a whole span;
+// the last items of a launch (at most ROX_TAIL_ITEMS_MAX, about half a warp round) are
+// split into their parts, taken by different warps: each part stores its sum in the tail
+// scratch and the last of them to finish adds the parts in the same order. The result is
+// the same either way, so it depends neither on the split nor on the launch grid.
+#define ROX_PARTS 4
+#define ROX_TAIL_ITEMS_MAX 2048
+
 struct RoxVoigtArgs {
   RoxWsHeader* hdr;
+  float* tail_part;                 // [n_items - n_whole][ROX_PARTS][ROX_SPAN] part sums
+  int32_t* tail_cnt;                // [n_items - n_whole] parts finished (zeroed per launch)
   int32_t n_jobs;
-  int32_t n_items;
+  int32_t n_items;                  // items (spans over all jobs); the last n_items - n_whole split
+  int32_t n_whole;
+  int32_t n_queue;                  // queue entries: n_whole + (n_items - n_whole) * ROX_PARTS
   int32_t item_end[ROX_MAX_JOBS];   // item_end[k] = spans of jobs 0..k
   RoxListDev list[ROX_MAX_LISTS];
   RoxJobDev job[ROX_MAX_JOBS];
@@ -116,3 +129,7 @@ struct RoxStrengthJobs {
 static_assert(sizeof(RoxStrengthJobs) < 32000, "kernel parameter space");
 
 static inline size_t rox_align256(size_t b) { return (b + 255) & ~(size_t)255; }
+// tail scratch of a workspace: `cap` items x ROX_PARTS x ROX_SPAN floats, then cap counters
+static inline size_t rox_tail_bytes(long long cap) {
+  return rox_align256((size_t)cap * ROX_PARTS * ROX_SPAN * sizeof(float)) + rox_align256((size_t)cap * 4);
+}

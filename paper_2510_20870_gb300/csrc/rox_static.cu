@@ -9,7 +9,7 @@
 
 // Size of the static scratch: enough for ROX_STATIC_MAX_LINES lines on a grid of
 // ROX_STATIC_MAX_GRID points at one (P,T) point (include/rox.h).
-#define ROX_STATIC_BYTES (8u << 20)
+#define ROX_STATIC_BYTES (16u << 20)
 #define ROX_STATIC_MAX_DEVICES 64
 
 // Library-owned scratch. Every GPU that loads the library keeps this array until exit.

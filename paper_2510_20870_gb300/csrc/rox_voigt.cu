@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
   __shared__ float s_S[ROX_WARPS][2][32];
   __shared__ Rec s_rec[ROX_WARPS][32];
   __shared__ float s_zacc[ROX_WARPS][ROX_SPAN];
+  __shared__ float s_tot[ROX_WARPS][ROX_SPAN];    // the span's sum over its parts
   __shared__ float s_daw[ROX_NDAW];
   __shared__ int s_status;
 
@@ -204,22 +205,27 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
   float(*S_st)[32] = s_S[w];
   Rec* rec = s_rec[w];
   float* zacc = s_zacc[w];
+  float* stot = s_tot[w];
   unsigned long long evals = 0;   // (line, point) pairs inside the cutoff and the job's window
 
   for (;;) {
-    int item = 0, k = 0;
+    int q = 0, k = 0;
     if (lane == 0) {
-      item = atomicAdd(&A.hdr->work_counter, 1);
-      int lo_k = 0, hi_k = A.n_jobs - 1;           // first job with item_end > item
+      q = atomicAdd(&A.hdr->work_counter, 1);
+      const int it = q < A.n_whole ? q : A.n_whole + (q - A.n_whole) / ROX_PARTS;
+      int lo_k = 0, hi_k = A.n_jobs - 1;           // first job with item_end > it
       while (lo_k < hi_k) {
         const int mid = (lo_k + hi_k) >> 1;
-        if (A.item_end[mid] > item) hi_k = mid; else lo_k = mid + 1;
+        if (A.item_end[mid] > it) hi_k = mid; else lo_k = mid + 1;
       }
       k = lo_k;
     }
-    item = __shfl_sync(0xffffffffu, item, 0);
+    q = __shfl_sync(0xffffffffu, q, 0);
     k = __shfl_sync(0xffffffffu, k, 0);
-    if (item >= A.n_items) break;
+    if (q >= A.n_queue) break;
+    // queue entry -> item and part (-1: the whole span, all parts in order)
+    const int item = q < A.n_whole ? q : A.n_whole + (q - A.n_whole) / ROX_PARTS;
+    const int part = q < A.n_whole ? -1 : (q - A.n_whole) % ROX_PARTS;
     const RoxJobDev& J = A.job[k];
     const RoxListDev& Lst = A.list[J.list];
     const int local = item - (k > 0 ? A.item_end[k - 1] : 0);
@@ -238,178 +244,212 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
     const int e = smax > 0.0 ? ilogb(smax) : 0;     // S32 holds S * 2^-e (FP32)
     const float* S_row = J.S32 - J.l0;              // indexed by line number
 
-    float acc[ROX_K], tot[ROX_K], cmp[ROX_K];
+    const long long nbat = hi > lo ? (hi - lo + 31) >> 5 : 0;
+    const int p_first = part < 0 ? 0 : part, p_last = part < 0 ? ROX_PARTS - 1 : part;
+    for (int p = p_first; p <= p_last; p++) {
+      const long long plo = lo + 32 * ((nbat * p) / ROX_PARTS);
+      const long long phi = min(hi, lo + 32 * ((nbat * (p + 1)) / ROX_PARTS));
+      float acc[ROX_K], tot[ROX_K], cmp[ROX_K];
 #pragma unroll
-    for (int m = 0; m < ROX_K; m++) { acc[m] = 0.f; tot[m] = 0.f; cmp[m] = 0.f; zacc[32 * m + lane] = 0.f; }
+      for (int m = 0; m < ROX_K; m++) { acc[m] = 0.f; tot[m] = 0.f; cmp[m] = 0.f; zacc[32 * m + lane] = 0.f; }
 
-    // stage batch 0; widths go through registers one batch ahead
-    float gref = 0.f, nt = 0.f;
-    if (lo + lane < hi) {
-      cp_async16(&geo_st[0][lane], &Lst.geo[lo + lane]);
-      cp_async4(&S_st[0][lane], &S_row[lo + lane]);
-      gref = load_width(Lst.gamma_ref, f16, lo + lane);
-      nt = load_width(Lst.n_t, f16, lo + lane);
-    }
-    cp_async_commit();
-    int nb = 0;
-    for (long long b0 = lo; b0 < hi; b0 += 32, nb++) {
-      const int cnt = (int)min((long long)32, hi - b0);
-      const int buf = nb & 1;
-      float gref_n = 0.f, nt_n = 0.f;
-      if (b0 + 32 + lane < hi) {
-        cp_async16(&geo_st[buf ^ 1][lane], &Lst.geo[b0 + 32 + lane]);
-        cp_async4(&S_st[buf ^ 1][lane], &S_row[b0 + 32 + lane]);
-        gref_n = load_width(Lst.gamma_ref, f16, b0 + 32 + lane);
-        nt_n = load_width(Lst.n_t, f16, b0 + 32 + lane);
+      // stage batch 0; widths go through registers one batch ahead
+      float gref = 0.f, nt = 0.f;
+      if (plo + lane < phi) {
+        cp_async16(&geo_st[0][lane], &Lst.geo[plo + lane]);
+        cp_async4(&S_st[0][lane], &S_row[plo + lane]);
+        gref = load_width(Lst.gamma_ref, f16, plo + lane);
+        nt = load_width(Lst.n_t, f16, plo + lane);
       }
       cp_async_commit();
-      cp_async_wait1();   // this lane's copies of the current batch have landed
+      int nb = 0;
+      for (long long b0 = plo; b0 < phi; b0 += 32, nb++) {
+        const int cnt = (int)min((long long)32, phi - b0);
+        const int buf = nb & 1;
+        float gref_n = 0.f, nt_n = 0.f;
+        if (b0 + 32 + lane < phi) {
+          cp_async16(&geo_st[buf ^ 1][lane], &Lst.geo[b0 + 32 + lane]);
+          cp_async4(&S_st[buf ^ 1][lane], &S_row[b0 + 32 + lane]);
+          gref_n = load_width(Lst.gamma_ref, f16, b0 + 32 + lane);
+          nt_n = load_width(Lst.n_t, f16, b0 + 32 + lane);
+        }
+        cp_async_commit();
+        cp_async_wait1();   // this lane's copies of the current batch have landed
 
-      // ---- per-line constants (lane <-> line b0 + lane)
-      Rec r;
-      if (lane < cnt) {
-        const float4 g = geo_st[buf][lane];
-        const float Sp = S_st[buf][lane];
-        const int jlo = __float_as_int(g.z), jhi = __float_as_int(g.w);
-        const int k0 = (int)g.x;
-        const float nu0f = Lst.nu_min_f + fmaf(g.x, dnu_f, g.y);
-        const float gG = nu0f * J.gG_fac;
-        const float gL = gref * exp2f(nt * J.l2_ratio) * J.p_fac;
-        const long long ov = min((long long)jhi, whi) - max((long long)jlo, wlo) + 1;
-        if (ov > 0) evals += (unsigned long long)ov;
-        const float gG2 = gG * gG, gL2 = gL * gL;
-        const float pY = Sp * gL * ROX_INV_PI;
-        const float invG = 1.0f / gG;
-        const float yv = gL * invG;
-        const rox_far fc = rox_far_coefs(yv);      // far-zone form of this line (rox_faddeeva.cuh)
-        // slow zone: |X| < sqrt(r2 gamma_G^2 - gamma_L^2), at least the precision margin
-        float hz = sqrtf(fmaxf(0.0f, fc.r2 * gG2 - gL2));
-        // zone |z| < 6.5 not widened by the margin: the core forms cover all of it
-        const bool core_only = fc.r2 == ROX_S_PADE && hz >= margin_cm;
-        hz = fmaxf(hz, margin_cm);
-        const float hzg = fminf(hz / dnu_f * 1.0001f, 8.0e6f);
-        const float f = g.y / dnu_f;
-        const int zlo = k0 + (int)floorf(f - hzg) - 1;
-        const int zhi = k0 + (int)ceilf(f + hzg) + 1;
-        const bool covers = Aw >= jlo && Bw <= jhi;
-        const bool zoned = !(Bw < zlo || Aw > zhi);
-        const float vg = fc.alpha * gG2;
-        r.a = make_float4(g.x, g.y, vg, fc.beta * (gG2 * gG2));
-        r.b = make_float4(pY, pY * (fc.kappa * gG2), __uint_as_float((covers ? 1u : 0u) | (zoned ? 2u : 0u)),
-                          fmaf(hz, hz, vg));
-        r.c = make_float4(g.z, g.w, __int_as_float(zlo), __int_as_float(zhi));
-        r.d = make_float4(invG, yv, Sp * invG * ROX_INV_SQRT_PI, core_only ? 1.0f : 0.0f);
-      } else {   // padding record: contributes nothing
-        r.a = make_float4(0.f, 0.f, 1.f, 0.f);
-        r.b = make_float4(0.f, 0.f, __uint_as_float(0u), 0.f);
-        r.c = make_float4(__int_as_float(1), __int_as_float(0), __int_as_float(0), __int_as_float(0));
-        r.d = make_float4(1.f, 0.f, 0.f, 0.f);
-      }
-      rec[lane] = r;
-      gref = gref_n;
-      nt = nt_n;
-      __syncwarp();
+        // ---- per-line constants (lane <-> line b0 + lane)
+        Rec r;
+        if (lane < cnt) {
+          const float4 g = geo_st[buf][lane];
+          const float Sp = S_st[buf][lane];
+          const int jlo = __float_as_int(g.z), jhi = __float_as_int(g.w);
+          const int k0 = (int)g.x;
+          const float nu0f = Lst.nu_min_f + fmaf(g.x, dnu_f, g.y);
+          const float gG = nu0f * J.gG_fac;
+          const float gL = gref * exp2f(nt * J.l2_ratio) * J.p_fac;
+          const long long ov = min((long long)jhi, whi) - max((long long)jlo, wlo) + 1;
+          if (ov > 0) evals += (unsigned long long)ov;
+          const float gG2 = gG * gG, gL2 = gL * gL;
+          const float pY = Sp * gL * ROX_INV_PI;
+          const float invG = 1.0f / gG;
+          const float yv = gL * invG;
+          const rox_far fc = rox_far_coefs(yv);      // far-zone form of this line (rox_faddeeva.cuh)
+          // slow zone: |X| < sqrt(r2 gamma_G^2 - gamma_L^2), at least the precision margin
+          float hz = sqrtf(fmaxf(0.0f, fc.r2 * gG2 - gL2));
+          // zone |z| < 6.5 not widened by the margin: the core forms cover all of it
+          const bool core_only = fc.r2 == ROX_S_PADE && hz >= margin_cm;
+          hz = fmaxf(hz, margin_cm);
+          const float hzg = fminf(hz / dnu_f * 1.0001f, 8.0e6f);
+          const float f = g.y / dnu_f;
+          const int zlo = k0 + (int)floorf(f - hzg) - 1;
+          const int zhi = k0 + (int)ceilf(f + hzg) + 1;
+          const bool covers = Aw >= jlo && Bw <= jhi;
+          const bool zoned = !(Bw < zlo || Aw > zhi);
+          const float vg = fc.alpha * gG2;
+          r.a = make_float4(g.x, g.y, vg, fc.beta * (gG2 * gG2));
+          r.b = make_float4(pY, pY * (fc.kappa * gG2), __uint_as_float((covers ? 1u : 0u) | (zoned ? 2u : 0u)),
+                            fmaf(hz, hz, vg));
+          r.c = make_float4(g.z, g.w, __int_as_float(zlo), __int_as_float(zhi));
+          r.d = make_float4(invG, yv, Sp * invG * ROX_INV_SQRT_PI, core_only ? 1.0f : 0.0f);
+        } else {   // padding record: contributes nothing
+          r.a = make_float4(0.f, 0.f, 1.f, 0.f);
+          r.b = make_float4(0.f, 0.f, __uint_as_float(0u), 0.f);
+          r.c = make_float4(__int_as_float(1), __int_as_float(0), __int_as_float(0), __int_as_float(0));
+          r.d = make_float4(1.f, 0.f, 0.f, 0.f);
+        }
+        rec[lane] = r;
+        gref = gref_n;
+        nt = nt_n;
+        __syncwarp();
 
-      // ---- pass 1: far formula. Clean lines (window covers the span, no slow zone in it) in
-      // unmasked pairs; covering lines with a slow zone in masked pairs; window-edge lines in
-      // pairs with window masks. The orders are fixed, so the sum is reproducible.
-      const unsigned cls = __float_as_uint(r.b.z);
-      const bool live = lane < cnt;
-      unsigned cmask = __ballot_sync(0xffffffffu, live && cls == 1u);
-      unsigned zmask = __ballot_sync(0xffffffffu, live && cls == 3u);
-      const unsigned emask = __ballot_sync(0xffffffffu, live && !(cls & 1u));
-      const unsigned pmask = __ballot_sync(0xffffffffu, live && (cls & 2u));
-      while (cmask) {
-        const int i0 = __ffs(cmask) - 1;
-        cmask &= cmask - 1;
-        const float4 a0 = rec[i0].a, b0v = rec[i0].b;
-        const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y);
-        if (cmask) {
-          const int i1 = __ffs(cmask) - 1;
+        // ---- pass 1: far formula. Clean lines (window covers the span, no slow zone in it) in
+        // unmasked pairs; covering lines with a slow zone in masked pairs; window-edge lines in
+        // pairs with window masks. The orders are fixed, so the sum is reproducible.
+        const unsigned cls = __float_as_uint(r.b.z);
+        const bool live = lane < cnt;
+        unsigned cmask = __ballot_sync(0xffffffffu, live && cls == 1u);
+        unsigned zmask = __ballot_sync(0xffffffffu, live && cls == 3u);
+        const unsigned emask = __ballot_sync(0xffffffffu, live && !(cls & 1u));
+        const unsigned pmask = __ballot_sync(0xffffffffu, live && (cls & 2u));
+        while (cmask) {
+          const int i0 = __ffs(cmask) - 1;
           cmask &= cmask - 1;
-          const float4 a1 = rec[i1].a, b1v = rec[i1].b;
-          const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
+          const float4 a0 = rec[i0].a, b0v = rec[i0].b;
+          const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y);
+          if (cmask) {
+            const int i1 = __ffs(cmask) - 1;
+            cmask &= cmask - 1;
+            const float4 a1 = rec[i1].a, b1v = rec[i1].b;
+            const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
 #pragma unroll
-          for (int m = 0; m < ROX_K; m++) {
-            const float x0 = fmaf((float)(32 * m), dnu_f, X0);
-            const float x1 = fmaf((float)(32 * m), dnu_f, X1);
-            const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
-            const float d0 = fmaf(t0, t0, a0.w), d1 = fmaf(t1, t1, a1.w);
-            const float n0 = fmaf(t0, b0v.x, b0v.y), n1 = fmaf(t1, b1v.x, b1v.y);
-            const float dd = d0 * d1;
-            const float nn = fmaf(n1, d0, n0 * d1);
-            acc[m] = fmaf(nn, rox_rcp(dd), acc[m]);
+            for (int m = 0; m < ROX_K; m++) {
+              const float x0 = fmaf((float)(32 * m), dnu_f, X0);
+              const float x1 = fmaf((float)(32 * m), dnu_f, X1);
+              const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
+              const float d0 = fmaf(t0, t0, a0.w), d1 = fmaf(t1, t1, a1.w);
+              const float n0 = fmaf(t0, b0v.x, b0v.y), n1 = fmaf(t1, b1v.x, b1v.y);
+              const float dd = d0 * d1;
+              const float nn = fmaf(n1, d0, n0 * d1);
+              acc[m] = fmaf(nn, rox_rcp(dd), acc[m]);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < ROX_K; m++) acc[m] += far_term(fmaf((float)(32 * m), dnu_f, X0), a0, b0v);
           }
-        } else {
-#pragma unroll
-          for (int m = 0; m < ROX_K; m++) acc[m] += far_term(fmaf((float)(32 * m), dnu_f, X0), a0, b0v);
         }
-      }
-      while (zmask) {
-        const int i0 = __ffs(zmask) - 1;
-        zmask &= zmask - 1;
-        const float4 a0 = rec[i0].a, b0v = rec[i0].b;
-        const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y);
-        if (zmask) {
-          const int i1 = __ffs(zmask) - 1;
+        while (zmask) {
+          const int i0 = __ffs(zmask) - 1;
           zmask &= zmask - 1;
-          const float4 a1 = rec[i1].a, b1v = rec[i1].b;
-          const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
+          const float4 a0 = rec[i0].a, b0v = rec[i0].b;
+          const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y);
+          if (zmask) {
+            const int i1 = __ffs(zmask) - 1;
+            zmask &= zmask - 1;
+            const float4 a1 = rec[i1].a, b1v = rec[i1].b;
+            const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
+#pragma unroll
+            for (int m = 0; m < ROX_K; m++) {
+              const float x0 = fmaf((float)(32 * m), dnu_f, X0);
+              const float x1 = fmaf((float)(32 * m), dnu_f, X1);
+              const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
+              const bool f0 = t0 >= b0v.w, f1 = t1 >= b1v.w;   // outside the slow zone
+              const float d0 = f0 ? fmaf(t0, t0, a0.w) : 1.0f, d1 = f1 ? fmaf(t1, t1, a1.w) : 1.0f;
+              const float n0 = f0 ? fmaf(t0, b0v.x, b0v.y) : 0.0f;
+              const float n1 = f1 ? fmaf(t1, b1v.x, b1v.y) : 0.0f;
+              const float dd = d0 * d1;
+              const float nn = fmaf(n1, d0, n0 * d1);
+              acc[m] = fmaf(nn, rox_rcp(dd), acc[m]);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < ROX_K; m++) acc[m] += masked_far(fmaf((float)(32 * m), dnu_f, X0), a0, b0v);
+          }
+        }
+        for (unsigned em = emask; em;) {
+          const int i0 = __ffs(em) - 1;
+          em &= em - 1;
+          if (!em) {
+            edge_line(rec[i0].a, rec[i0].b, rec[i0].c, Aw, lane, Jf, dnu_f, acc);
+            break;
+          }
+          const int i1 = __ffs(em) - 1;
+          em &= em - 1;
+          edge_pair(rec[i0], rec[i1], Aw, lane, Jf, dnu_f, acc);
+        }
+        // ---- pass 2: the points each zoned line left out of pass 1, full Faddeeva forms
+        for (unsigned pm = pmask; pm; pm &= pm - 1) {
+          const Rec rq = rec[__ffs(pm) - 1];
+          zone_line(rq, Aw, lane, Jf, dnu_f, s_daw, zacc);
+        }
+        __syncwarp();
+        // compensated (Kahan) accumulation of the partial sums, every 4 batches
+        if ((nb & 3) == 3 || b0 + 32 >= phi) {
 #pragma unroll
           for (int m = 0; m < ROX_K; m++) {
-            const float x0 = fmaf((float)(32 * m), dnu_f, X0);
-            const float x1 = fmaf((float)(32 * m), dnu_f, X1);
-            const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
-            const bool f0 = t0 >= b0v.w, f1 = t1 >= b1v.w;   // outside the slow zone
-            const float d0 = f0 ? fmaf(t0, t0, a0.w) : 1.0f, d1 = f1 ? fmaf(t1, t1, a1.w) : 1.0f;
-            const float n0 = f0 ? fmaf(t0, b0v.x, b0v.y) : 0.0f;
-            const float n1 = f1 ? fmaf(t1, b1v.x, b1v.y) : 0.0f;
-            const float dd = d0 * d1;
-            const float nn = fmaf(n1, d0, n0 * d1);
-            acc[m] = fmaf(nn, rox_rcp(dd), acc[m]);
+            const float yk = acc[m] - cmp[m];
+            const float tk = tot[m] + yk;
+            cmp[m] = (tk - tot[m]) - yk;
+            tot[m] = tk;
+            acc[m] = 0.f;
           }
-        } else {
+        }
+      }
+      cp_async_wait0();
+      // fold in the pass-2 (near-centre) sums
 #pragma unroll
-          for (int m = 0; m < ROX_K; m++) acc[m] += masked_far(fmaf((float)(32 * m), dnu_f, X0), a0, b0v);
-        }
+      for (int m = 0; m < ROX_K; m++) {
+        const float yk = zacc[32 * m + lane] - cmp[m];
+        const float tk = tot[m] + yk;
+        cmp[m] = (tk - tot[m]) - yk;
+        tot[m] = tk;
       }
-      for (unsigned em = emask; em;) {
-        const int i0 = __ffs(em) - 1;
-        em &= em - 1;
-        if (!em) {
-          edge_line(rec[i0].a, rec[i0].b, rec[i0].c, Aw, lane, Jf, dnu_f, acc);
-          break;
-        }
-        const int i1 = __ffs(em) - 1;
-        em &= em - 1;
-        edge_pair(rec[i0], rec[i1], Aw, lane, Jf, dnu_f, acc);
-      }
-      // ---- pass 2: the points each zoned line left out of pass 1, full Faddeeva forms
-      for (unsigned pm = pmask; pm; pm &= pm - 1) {
-        const Rec rq = rec[__ffs(pm) - 1];
-        zone_line(rq, Aw, lane, Jf, dnu_f, s_daw, zacc);
+      if (part >= 0) {           // a split item: this part's sum goes to the tail scratch
+        float* dst = A.tail_part + ((size_t)(item - A.n_whole) * ROX_PARTS + p) * ROX_SPAN;
+#pragma unroll
+        for (int m = 0; m < ROX_K; m++) __stcg(&dst[32 * m + lane], tot[m]);
+      } else {
+#pragma unroll
+        for (int m = 0; m < ROX_K; m++) stot[32 * m + lane] = p == 0 ? tot[m] : stot[32 * m + lane] + tot[m];
       }
       __syncwarp();
-      // compensated (Kahan) accumulation of the partial sums, every 4 batches
-      if ((nb & 3) == 3 || b0 + 32 >= hi) {
+    }   // parts
+
+    if (part >= 0) {
+      // the last part to finish adds the parts in order (the same sum as a whole item)
+      __threadfence();
+      __syncwarp();
+      int done = 0;
+      if (lane == 0) done = atomicAdd(&A.tail_cnt[item - A.n_whole], 1);
+      done = __shfl_sync(0xffffffffu, done, 0);
+      if (done != ROX_PARTS - 1) continue;
+      __threadfence();
+      const float* src = A.tail_part + (size_t)(item - A.n_whole) * ROX_PARTS * ROX_SPAN;
 #pragma unroll
-        for (int m = 0; m < ROX_K; m++) {
-          const float yk = acc[m] - cmp[m];
-          const float tk = tot[m] + yk;
-          cmp[m] = (tk - tot[m]) - yk;
-          tot[m] = tk;
-          acc[m] = 0.f;
-        }
+      for (int m = 0; m < ROX_K; m++) {
+        float v = __ldcg(&src[32 * m + lane]);
+#pragma unroll
+        for (int pp = 1; pp < ROX_PARTS; pp++) v = v + __ldcg(&src[pp * ROX_SPAN + 32 * m + lane]);
+        stot[32 * m + lane] = v;
       }
-    }
-    cp_async_wait0();
-    // fold in the pass-2 (near-centre) sums
-#pragma unroll
-    for (int m = 0; m < ROX_K; m++) {
-      const float yk = zacc[32 * m + lane] - cmp[m];
-      const float tk = tot[m] + yk;
-      cmp[m] = (tk - tot[m]) - yk;
-      tot[m] = tk;
     }
     // ---- write the span once (its part inside the job's window)
     float* out = J.sigma - J.first;
@@ -417,7 +457,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
     for (int m = 0; m < ROX_K; m++) {
       const long long j = (long long)Aw + 32 * m + lane;
       if (j >= wlo && j <= whi) {
-        const float v = ldexpf(tot[m], e);
+        const float v = ldexpf(stot[32 * m + lane], e);
         out[j] = (J.flags & ROX_ACCUMULATE) ? out[j] + v : v;
       }
     }

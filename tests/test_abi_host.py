@@ -80,3 +80,11 @@ def test_partition_function_host_helper():
     with pytest.raises(ValueError):
         q(49.0)
     assert PartitionFunction(("analytic", 0.05))(400.0) == pytest.approx(0.05 * 8000.0)
+
+
+def test_static_scratch_holds_the_largest_static_problem():
+    """rox_xsec_static runs rox_xsec in a fixed 16 MiB array: the workspace of its largest
+    accepted problem (ROX_STATIC_MAX_LINES lines, ROX_STATIC_MAX_GRID points, one T) fits."""
+    from paper_2510_20870_gb300 import _binding as b
+    need = b.rox_xsec_workspace_size(262144, (0.0, 0.01, 1 << 21), 1)
+    assert 0 < need <= 16 << 20, need
