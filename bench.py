@@ -34,7 +34,7 @@ import rox_synth as rs  # noqa: E402
 FLOPS_PER_EVAL = 11.0   # far-wing pair formula: 10 FFMA + 2 FMUL per 2 evaluations (+ 1 MUFU rcp)
 # DRAM bytes per Voigt launch on the full exomol workload: ncu dram__bytes_read + write of the
 # 2e6-line case (profiles/k_voigt_exomol_2e6lines.md), scaled by evaluations (x5.0)
-VOIGT_TRAFFIC_BYTES = 2.975e8
+VOIGT_TRAFFIC_BYTES = 3.035e8
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "Voigt line-profile evals/s"
