@@ -25,6 +25,12 @@ Readings where the paper is silent (all listed in the design doc as well):
   R7  Point sampling at grid nodes nu_j = nu_min + j*dnu, j = 0..n-1 (computed, not accumulated).
   R8  sigma_j = sum over lines in ascending order of S_i V_ij (float64).
   R9  Partition function: analytic Q(T) = a T^1.5, or a 1 K table interpolated linearly.
+  R14 User-provided grids (section "Similar tools": any wavelength or wavenumber grid, e.g.
+      a fixed resolution R = lambda/dlambda): the nodes nu_k are given as float64 values,
+      strictly increasing; R6 and R8 apply with nu_k in place of nu_min + j*dnu, i.e. a line
+      contributes to node k iff abs(nu_k - nu0) <= cutoff in float64.
+      A fixed-resolution grid has nu_k = nu_lo * (1 + 1/R)^k (constant nu/dnu, hence constant
+      lambda/dlambda), k = 0..K with K the largest index keeping nu_k <= nu_hi.
 """
 import numpy as np
 from scipy.special import wofz
@@ -34,6 +40,7 @@ __all__ = [
     "partition_function", "line_strength", "doppler_width", "lorentz_width",
     "voigt_profile", "grid_nodes", "window_indices", "count_evals",
     "xsec_bruteforce", "xsec_windowed", "xsec_points", "xsec_window", "sort_lines",
+    "fixed_resolution_nodes", "node_windows", "xsec_nodes", "xsec_nodes_bruteforce",
 ]
 
 # R1: CODATA 2018 exact SI values where defined
@@ -219,4 +226,86 @@ def xsec_points(lines_sorted, grid, js, P_bar, T, Q_T, Q_ref, mass_amu, cutoff):
     out = np.empty(len(js), dtype=np.float64)
     for k, j in enumerate(js):
         out[k] = xsec_window(lines_sorted, grid, int(j), int(j) + 1, P_bar, T, Q_T, Q_ref, mass_amu, cutoff)[0]
+    return out
+
+
+# ---------------------------------------------------------------- R14: user-provided grids
+def fixed_resolution_nodes(nu_lo, nu_hi, R):
+    """R14. Nodes nu_k = nu_lo * (1 + 1/R)^k, k = 0..K, K = floor(log(nu_hi/nu_lo)/log(1 + 1/R))
+    (each nu_k is one power and one multiply, not accumulated)."""
+    q = 1.0 + 1.0 / float(R)
+    K = int(np.floor(np.log(float(nu_hi) / float(nu_lo)) / np.log(q)))
+    while K >= 0 and nu_lo * q ** K > nu_hi:
+        K -= 1
+    k = np.arange(K + 1, dtype=np.float64)
+    return float(nu_lo) * np.power(q, k)
+
+
+def node_windows(nu0, nodes, cutoff):
+    """R14 windows: per line, the first node k with nodes[k] - nu0 >= -cutoff and the last
+    with nodes[k] - nu0 <= cutoff (float64 differences as written; jhi < jlo when the line
+    reaches no node). Binary search, valid because the difference is monotone in k."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    nu0 = np.atleast_1d(np.asarray(nu0, dtype=np.float64))
+    n = nodes.size
+    jlo = np.empty(nu0.size, dtype=np.int64)
+    jhi = np.empty(nu0.size, dtype=np.int64)
+    for i, c in enumerate(nu0):
+        a, b = 0, n                       # first k in [0, n] with nodes[k] - c >= -cutoff
+        while a < b:
+            mid = (a + b) // 2
+            if nodes[mid] - c >= -cutoff:
+                b = mid
+            else:
+                a = mid + 1
+        jlo[i] = a
+        a, b = 0, n                       # first k with nodes[k] - c > cutoff, minus one
+        while a < b:
+            mid = (a + b) // 2
+            if nodes[mid] - c > cutoff:
+                b = mid
+            else:
+                a = mid + 1
+        jhi[i] = a - 1
+    return jlo, jhi
+
+
+def xsec_nodes_bruteforce(lines, nodes, P_bar, T, Q_T, Q_ref, mass_amu, cutoff):
+    """R8 with R14: every line against every node, explicit cutoff test, lines in the given
+    order. Tiny inputs only."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    S, gG, gL = _line_params(lines, P_bar, T, Q_T, Q_ref, mass_amu)
+    sigma = np.zeros(nodes.size, dtype=np.float64)
+    nu0 = np.asarray(lines["nu0"], dtype=np.float64)
+    for i in range(nu0.size):
+        d = nodes - nu0[i]
+        contrib = S[i] * voigt_profile(d, gG[i], gL[i])
+        sigma += np.where(np.abs(d) <= cutoff, contrib, 0.0)
+    return sigma
+
+
+def xsec_nodes(lines_sorted, nodes, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, ks=None):
+    """R8 with R14 at nodes[ks] (all nodes if ks is None): for each node, the lines whose
+    nu0 lies within cutoff (plus a margin) are cut from the sorted list, the cutoff test
+    decides each pair, and the lines are added in ascending order (so the result equals the
+    brute force on the sorted list bit for bit)."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    ks = np.arange(nodes.size) if ks is None else np.asarray(ks)
+    nu0 = np.asarray(lines_sorted["nu0"], dtype=np.float64)
+    S, gG, gL = _line_params(lines_sorted, P_bar, T, Q_T, Q_ref, mass_amu)
+    out = np.zeros(ks.size, dtype=np.float64)
+    # lines are sorted, so each node's candidates are one contiguous range
+    a_all = np.searchsorted(nu0, nodes[ks] - cutoff * (1 + 1e-12) - 1e-9, side="left")
+    b_all = np.searchsorted(nu0, nodes[ks] + cutoff * (1 + 1e-12) + 1e-9, side="right")
+    for q, k in enumerate(ks):
+        a, b = int(a_all[q]), int(b_all[q])
+        if a >= b:
+            continue
+        d = nodes[k] - nu0[a:b]
+        m = np.abs(d) <= cutoff
+        contrib = S[a:b][m] * voigt_profile(d[m], gG[a:b][m], gL[a:b][m])
+        acc = 0.0
+        for v in contrib:                 # ascending line order, one add at a time
+            acc += v
+        out[q] = acc
     return out

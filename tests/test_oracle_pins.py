@@ -245,12 +245,65 @@ def pin_points_equal_full(o):
     assert np.array_equal(o.xsec_window(L, GRID, 123, 4567, *ARGS), full[123:4567])
 
 
+# ---------------------------------------------------------------- user-provided grids (R14)
+def pin_nodes_uniform_equals_windowed(o):
+    # a uniform grid handed over as explicit nodes gives the windowed sum bit for bit
+    L = _small(n=60)
+    full = o.xsec_windowed(L, GRID, *ARGS)
+    nodes = o.grid_nodes(*GRID)
+    ks = np.array([0, 1, 17, 2500, 2501, 9999, 31337, 49999, 50000])
+    assert np.array_equal(o.xsec_nodes(L, nodes, *ARGS, ks=ks), full[ks])
+
+
+def pin_nodes_bruteforce(o):
+    # irregular nodes (clusters and gaps), lines inside and outside the node range
+    rng = np.random.default_rng(11)
+    nodes = np.sort(np.concatenate([rng.uniform(2000, 2500, 700), 2200 + rng.uniform(0, 0.05, 300)]))
+    nodes = np.unique(nodes)
+    L = _small(n=25)
+    cut = 3.0
+    brute = o.xsec_nodes_bruteforce(L, nodes, *ARGS[:5], cut)
+    assert np.array_equal(o.xsec_nodes(L, nodes, *ARGS[:5], cut), brute)
+    assert np.count_nonzero(brute) > 100
+
+
+def pin_node_windows(o):
+    nodes = o.grid_nodes(*GRID)
+    rng = np.random.default_rng(12)
+    nu0 = np.concatenate([rng.uniform(1950, 2550, 200), [2000.0 - 25.0, 2500.0 + 25.0, 1900.0, 2600.0]])
+    jlo, jhi = o.node_windows(nu0, nodes, 25.0)
+    ulo, uhi = o.window_indices(nu0, *GRID, 25.0)
+    n = GRID[2]
+    assert np.array_equal(jlo, np.clip(ulo, 0, n)) and np.array_equal(jhi, np.clip(uhi, -1, n - 1))
+    irr = np.unique(rng.uniform(0, 100, 500))
+    for c in rng.uniform(-10, 110, 50):
+        inside = np.nonzero(np.abs(irr - c) <= 7.5)[0]
+        lo, hi = o.node_windows([c], irr, 7.5)
+        if inside.size:
+            assert (lo[0], hi[0]) == (inside[0], inside[-1])
+        else:
+            assert hi[0] < lo[0]
+
+
+def pin_fixed_resolution(o):
+    R = 1.0e5
+    nodes = o.fixed_resolution_nodes(2000.0, 2500.0, R)
+    ratio = nodes[1:] / nodes[:-1]
+    assert np.allclose(ratio, 1.0 + 1.0 / R, rtol=1e-14, atol=0)
+    lam = 1.0e4 / nodes                      # micron, descending
+    res = lam[1:] / (lam[:-1] - lam[1:])     # lambda / dlambda of each neighbouring pair
+    assert np.allclose(res, R, rtol=1e-8, atol=0)
+    assert nodes[0] == 2000.0 and nodes[-1] <= 2500.0 < nodes[-1] * (1.0 + 1.0 / R)
+    assert nodes.size == int(math.floor(math.log(2500.0 / 2000.0) / math.log1p(1.0 / R))) + 1
+
+
 PINS = [pin_c2, pin_hitran_at_tref, pin_exomol_from_oscillator_strength, pin_hitran_exomol_consistency,
         pin_partition_table, pin_doppler_published, pin_lorentz_closed_forms, pin_voigt_gaussian_limit,
         pin_voigt_centre_erfcx, pin_voigt_lorentz_limit, pin_voigt_convolution_quadrature,
         pin_voigt_scipy_profile, pin_voigt_normalisation, pin_brute_equals_windowed, pin_single_line,
         pin_linearity_and_permutation, pin_grid_shift, pin_cutoff_inclusive, pin_count_evals_bruteforce,
-        pin_points_equal_full]
+        pin_points_equal_full, pin_nodes_uniform_equals_windowed, pin_nodes_bruteforce, pin_node_windows,
+        pin_fixed_resolution]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -322,3 +375,19 @@ def test_mutation_sum_order_index(monkeypatch):
     real = orc.grid_nodes
     monkeypatch.setattr(orc, "grid_nodes", lambda nu_min, dnu, n, j=None: real(nu_min, dnu, n, j) + dnu)
     assert _fails(pin_single_line) or _fails(pin_cutoff_inclusive)
+
+
+def test_mutation_node_cutoff_exclusive(monkeypatch):
+    real = orc.node_windows
+
+    def wrong(nu0, nodes, cutoff):
+        jlo, jhi = real(nu0, nodes, cutoff * (1 - 1e-9))   # drops nodes exactly at the cutoff
+        return jlo, jhi
+    monkeypatch.setattr(orc, "node_windows", wrong)
+    assert _fails(pin_node_windows)
+
+
+def test_mutation_nodes_shifted(monkeypatch):
+    real = orc.xsec_nodes
+    monkeypatch.setattr(orc, "xsec_nodes", lambda L, nodes, *a, **k: real(L, np.asarray(nodes) + 1e-3, *a, **k))
+    assert _fails(pin_nodes_uniform_equals_windowed) and _fails(pin_nodes_bruteforce)
