@@ -49,6 +49,7 @@ extern "C" {
 #define ROX_ETIMEOUT 4    /* a bounded device-side wait ran out (reported by rox_ws_status) */
 #define ROX_EUNSORTED 5   /* line list not in ascending nu0 (reported by rox_ws_status) */
 #define ROX_ERANGE 6      /* a size beyond a documented limit */
+#define ROX_EGRID 7       /* user-provided nodes not finite or not strictly increasing (rox_ws_status) */
 
 /* line-list conventions */
 #define ROX_HITRAN 0      /* s_or_a = S_ref at 296 K (cm/molecule) */
@@ -102,6 +103,14 @@ typedef struct rox_grid {
   double dnu;
   int64_t n;
 } rox_grid;
+
+/* User-provided grid (paper, "Similar tools": cross-sections on any wavelength or wavenumber
+ * grid, e.g. one of fixed resolution R = lambda/dlambda): n nodes nu[0..n-1] (cm^-1, DEVICE,
+ * double), finite and strictly increasing. */
+typedef struct rox_nodes {
+  const double* nu;
+  int64_t n;
+} rox_nodes;
 
 /* Message of the last error on this thread ("" if none). Never NULL. */
 const char* rox_last_error(void);
@@ -180,9 +189,34 @@ int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double 
              double Q_T, double Q_ref, double mass_amu, double cutoff, float* sigma_out,
              void* ws, size_t ws_bytes, void* stream);
 
+/* a4/a5 on user-provided nodes (paper, "Similar tools": any user-provided wavelength or
+ * wavenumber grid, which fixes the resolving power R = lambda/dlambda): rox_xsec_batch with the
+ * uniform grid replaced by nodes nu[0..n-1]. A line contributes to node k iff
+ * |nu[k] - nu0| <= cutoff, the difference taken once in double precision; sigma_out is
+ * [n_pt][nodes->n]. Arguments, flags, ordering and precision as rox_xsec_batch, except that the
+ * cutoff only needs 0 < cutoff <= 4000 cm^-1. The nodes are checked on the device: if they are
+ * not finite or not strictly increasing, nothing is written and rox_ws_status returns
+ * ROX_EGRID. ws: device workspace of rox_xsec_nodes_workspace_size(lines->n, nodes->n,
+ * n_temps) bytes (n_temps as for rox_xsec_batch); it includes each node's offset from the
+ * first node of its ROX_SPAN-node span, the kernel's exact stand-in for the index
+ * decomposition of a uniform grid. */
+size_t rox_xsec_nodes_workspace_size(int64_t n_lines, int64_t n_nodes, int n_temps);
+int rox_xsec_nodes_batch(const rox_lines* lines, const rox_nodes* nodes, int n_pt,
+                         const double* P_bar, const double* T, const double* Q_T, double Q_ref,
+                         double mass_amu, double cutoff, unsigned flags, float* sigma_out,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* a3 windows on user-provided nodes: per sorted line, the first node with
+ * nu[k] - nu0 >= -cutoff (jlo, in [0, n]) and the last with nu[k] - nu0 <= cutoff (jhi, in
+ * [-1, n-1]; jhi < jlo when the line reaches no node), differences rounded once in double
+ * precision (binary searches). jlo, jhi: [n_lines] int32 (device). */
+int rox_node_windows(const double* nu0_sorted, int64_t n_lines, const rox_nodes* nodes,
+                     double cutoff, int32_t* jlo, int32_t* jhi, void* stream);
+
 /* Synchronises `stream` and returns the device-side status recorded in `ws` by the last
- * rox_xsec / rox_xsec_batch call that used it: ROX_OK, ROX_EUNSORTED (lines not in
- * ascending nu0: no sigma was written), or ROX_ETIMEOUT. If evals_out is not NULL it
+ * rox_xsec / rox_xsec_batch / rox_xsec_nodes_batch call that used it: ROX_OK, ROX_EUNSORTED
+ * (lines not in ascending nu0: no sigma was written), ROX_EGRID (bad nodes: no sigma was
+ * written), or ROX_ETIMEOUT. If evals_out is not NULL it
  * receives the number of (line, grid point) pairs inside the cutoff summed over the
  * call's (P,T) points (the unit of work of the Voigt kernel). */
 int rox_ws_status(const void* ws, unsigned long long* evals_out, void* stream);

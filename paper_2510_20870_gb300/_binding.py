@@ -13,7 +13,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librox.so")
 
-ROX_OK, ROX_EINVAL, ROX_ENOMEM, ROX_ECUDA, ROX_ETIMEOUT, ROX_EUNSORTED, ROX_ERANGE = range(7)
+ROX_OK, ROX_EINVAL, ROX_ENOMEM, ROX_ECUDA, ROX_ETIMEOUT, ROX_EUNSORTED, ROX_ERANGE, ROX_EGRID = range(8)
 ROX_HITRAN, ROX_EXOMOL = 0, 1
 ROX_WIDTH_F32, ROX_WIDTH_F16 = 0, 1
 ROX_ACCUMULATE = 1
@@ -40,6 +40,10 @@ class RoxLinesBuf(ctypes.Structure):
 
 class RoxGrid(ctypes.Structure):
     _fields_ = [("nu_min", ctypes.c_double), ("dnu", ctypes.c_double), ("n", ctypes.c_int64)]
+
+
+class RoxNodes(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_void_p), ("n", ctypes.c_int64)]
 
 
 class RoxPrepared(ctypes.Structure):
@@ -80,6 +84,9 @@ def _load():
         "rox_prepare": (ctypes.c_int, [P, P, D, P, ctypes.c_size_t, P, P]),
         "rox_jobs_workspace_size": (ctypes.c_size_t, [P, ctypes.c_int]),
         "rox_xsec_jobs": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_size_t, P]),
+        "rox_xsec_nodes_workspace_size": (ctypes.c_size_t, [I64, I64, ctypes.c_int]),
+        "rox_xsec_nodes_batch": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P, ctypes.c_size_t, P]),
+        "rox_node_windows": (ctypes.c_int, [P, I64, P, D, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -186,6 +193,33 @@ def rox_xsec_batch(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_ou
     G = grid_struct(grid)
     _check(lib.rox_xsec_batch(ctypes.byref(L), ctypes.byref(G), n_pt, arr(*P_bar), arr(*T), arr(*Q_T), Q_ref,
                               mass_amu, cutoff, flags, _ptr(sigma_out), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def nodes_struct(nodes):
+    """rox_nodes from a CUDA float64 tensor of strictly increasing nodes (cm^-1)."""
+    if nodes.dtype != torch.float64:
+        raise TypeError("nodes must be float64")
+    return RoxNodes(_ptr(nodes).value, nodes.numel())
+
+
+def rox_xsec_nodes_workspace_size(n_lines, n_nodes, n_temps):
+    return lib.rox_xsec_nodes_workspace_size(n_lines, n_nodes, n_temps)
+
+
+def rox_xsec_nodes_batch(lines, nodes, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, flags=0, stream=None):
+    """Cross-sections on user-provided nodes (float64 CUDA tensor); sigma_out [n_pt][n_nodes]."""
+    n_pt = len(P_bar)
+    arr = ctypes.c_double * n_pt
+    L = lines_struct(lines)
+    N = nodes_struct(nodes)
+    _check(lib.rox_xsec_nodes_batch(ctypes.byref(L), ctypes.byref(N), n_pt, arr(*P_bar), arr(*T), arr(*Q_T), Q_ref,
+                                    mass_amu, cutoff, flags, _ptr(sigma_out), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def rox_node_windows(nu0, nodes, cutoff, jlo, jhi, stream=None):
+    N = nodes_struct(nodes)
+    _check(lib.rox_node_windows(_ptr(nu0), nu0.numel(), ctypes.byref(N), cutoff, _ptr(jlo), _ptr(jhi),
+                                _stream(stream)))
 
 
 def rox_xsec(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, stream=None):

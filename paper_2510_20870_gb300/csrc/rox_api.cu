@@ -30,10 +30,16 @@ cudaError_t rox_launch_tile_ranges_geo(const float4* geo, long long n_lines, lon
 size_t rox_sort_ws_bytes(long long n);
 cudaError_t rox_launch_sort(const rox_lines* in, const rox_lines_buf* out, int64_t* perm_out, void* ws,
                             cudaStream_t s);
-cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, cudaStream_t s);
+cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, cudaStream_t s);
+cudaError_t rox_launch_node_windows(const double* nu0, long long n_lines, const double* nodes, long long n,
+                                    double cutoff, int32_t* jlo, int32_t* jhi, float4* geo,
+                                    unsigned long long* evals, int32_t* unsorted, int32_t unsorted_value,
+                                    cudaStream_t s);
+cudaError_t rox_launch_node_offsets(const double* nodes, long long n, long long n_pad, float2* d, float2* base,
+                                    int32_t* status, int32_t bad_value, cudaStream_t s);
 void rox_fill_strength_consts(int convention, double T, double Q_T, double Q_ref, RoxStrengthJob* jb);
 cudaError_t rox_launch_strengths_jobs(const RoxStrengthJobs& J, long long max_count, cudaStream_t s);
-cudaError_t rox_voigt_blocks_per_sm(int* nb);
+cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes);
 cudaError_t rox_launch_faddeeva(const float* x, const float* y, float* out, long long n, cudaStream_t s);
 
 namespace {
@@ -89,6 +95,13 @@ int check_grid(const rox_grid* g) {
   return ROX_OK;
 }
 
+int check_nodes(const rox_nodes* g) {
+  if (!g || !g->nu) return fail(ROX_EINVAL, "nodes or nodes->nu is NULL");
+  if (g->n <= 0) return fail(ROX_EINVAL, "nodes->n = %lld <= 0", (long long)g->n);
+  if (g->n > ROX_MAX_GRID) return fail(ROX_ERANGE, "nodes->n = %lld above %d", (long long)g->n, ROX_MAX_GRID);
+  return ROX_OK;
+}
+
 int check_cutoff(double cutoff, const rox_grid* g) {
   if (!finite_pos(cutoff)) return fail(ROX_EINVAL, "cutoff must be > 0");
   if (cutoff > 4000.0) return fail(ROX_ERANGE, "cutoff %g above 4000 cm^-1", cutoff);
@@ -109,10 +122,12 @@ struct WsLayout {
   float* tail_part;
   int32_t* tail_cnt;
   long long tail_cap;
+  float2* node_d;      // user-provided nodes only: [n_tiles * ROX_SPAN] offsets, [n_tiles] bases
+  float2* span_base;
   size_t bytes;
 };
 
-WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps) {
+WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, bool nodes = false) {
   WsLayout w;
   char* base = (char*)ws;
   size_t off = 0;
@@ -133,27 +148,37 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps) {
   w.tail_part = (float*)(base + off);
   w.tail_cnt = (int32_t*)(base + off + rox_align256((size_t)w.tail_cap * ROX_PARTS * ROX_SPAN * sizeof(float)));
   off += rox_tail_bytes(w.tail_cap);
+  w.node_d = nullptr;
+  w.span_base = nullptr;
+  if (nodes) {
+    w.node_d = (float2*)(base + off);
+    off += rox_align256((size_t)nt * ROX_SPAN * sizeof(float2));
+    w.span_base = (float2*)(base + off);
+    off += rox_align256((size_t)nt * sizeof(float2));
+  }
   w.bytes = off;
   return w;
 }
 
-int g_voigt_blocks = 0;
-int g_voigt_device = -1;
+int g_voigt_blocks[2] = {0, 0};
+int g_voigt_device[2] = {-1, -1};
 
-int voigt_grid(int* out) {
+// persistent grid of the Voigt kernel on the current device (uniform grid or nodes)
+int voigt_grid(int* out, bool nodes = false) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
-  if (dev != g_voigt_device) {
+  const int v = nodes ? 1 : 0;
+  if (dev != g_voigt_device[v]) {
     int sms = 0, per = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_check(e, "cudaDeviceGetAttribute");
-    e = rox_voigt_blocks_per_sm(&per);
+    e = rox_voigt_blocks_per_sm(&per, nodes);
     if (e != cudaSuccess) return cuda_check(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    g_voigt_blocks = sms * (per > 0 ? per : 1);
-    g_voigt_device = dev;
+    g_voigt_blocks[v] = sms * (per > 0 ? per : 1);
+    g_voigt_device[v] = dev;
   }
-  *out = g_voigt_blocks;
+  *out = g_voigt_blocks[v];
   return ROX_OK;
 }
 
@@ -161,7 +186,8 @@ int voigt_grid(int* out) {
 // before each launch (the evaluation count keeps adding up). The last items of each launch,
 // up to tail_cap and half a round of the launch's warps, are split into their parts.
 int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* jobs, int n_jobs, RoxWsHeader* hdr,
-                      float* tail_part, int32_t* tail_cnt, long long tail_cap, int nblocks, cudaStream_t s) {
+                      float* tail_part, int32_t* tail_cnt, long long tail_cap, int nblocks, cudaStream_t s,
+                      bool nodes = false) {
   static thread_local RoxVoigtArgs A;   // ~30 KB of per-job parameters, passed by value
   A.hdr = hdr;
   A.tail_part = tail_part;
@@ -188,7 +214,7 @@ int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* job
     if (split > 0 && (rc = cuda_check(cudaMemsetAsync(tail_cnt, 0, (size_t)split * 4, s), "memset"))) return rc;
     if (j0 == 0 && g_prof_start && (rc = cuda_check(cudaEventRecord(g_prof_start, s), "cudaEventRecord"))) return rc;
     if (items == 0) continue;
-    if ((rc = cuda_check(rox_launch_voigt(A, blocks, s), "voigt kernel"))) return rc;
+    if ((rc = cuda_check(rox_launch_voigt(A, blocks, nodes, s), "voigt kernel"))) return rc;
   }
   if (g_prof_stop) return cuda_check(cudaEventRecord(g_prof_stop, s), "cudaEventRecord");
   return ROX_OK;
@@ -280,13 +306,18 @@ size_t rox_xsec_workspace_size(int64_t n_lines, const rox_grid* grid, int n_temp
   return ws_layout(nullptr, n_lines, grid->n, n_temps).bytes;
 }
 
-int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const double* P_bar, const double* T,
-                   const double* Q_T, double Q_ref, double mass_amu, double cutoff, unsigned flags, float* sigma_out,
-                   void* ws, size_t ws_bytes, void* stream) {
+}  // extern "C"
+
+namespace {
+// rox_xsec_batch and rox_xsec_nodes_batch: `grid` (uniform) or `nodes` (user-provided), the
+// other NULL; both checked by the caller.
+int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_nodes* nodes, int n_pt,
+                    const double* P_bar, const double* T, const double* Q_T, double Q_ref, double mass_amu,
+                    double cutoff, unsigned flags, float* sigma_out, void* ws, size_t ws_bytes, void* stream) {
   int rc = check_lines(lines, true, true);
   if (rc) return rc;
-  if ((rc = check_grid(grid))) return rc;
-  if ((rc = check_cutoff(cutoff, grid))) return rc;
+  const bool on_nodes = nodes != nullptr;
+  const long long n_grid = on_nodes ? nodes->n : grid->n;
   if (n_pt < 1 || n_pt > ROX_MAX_PT) return fail(ROX_EINVAL, "n_pt = %d outside [1, %d]", n_pt, ROX_MAX_PT);
   if (!P_bar || !T || !Q_T) return fail(ROX_EINVAL, "P_bar, T, Q_T host arrays required");
   if (!finite_pos(Q_ref) || !finite_pos(mass_amu)) return fail(ROX_EINVAL, "Q_ref and mass must be > 0");
@@ -312,21 +343,28 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
   }
   const int n_temps = (int)temps.size();
   if (!ws || ((uintptr_t)ws & 255)) return fail(ROX_EINVAL, "workspace NULL or not 256-byte aligned");
-  WsLayout w = ws_layout(ws, lines->n, grid->n, n_temps);
+  WsLayout w = ws_layout(ws, lines->n, n_grid, n_temps, on_nodes);
   if (ws_bytes < w.bytes) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.bytes);
 
   cudaStream_t s = (cudaStream_t)stream;
   int nblocks = 0;
-  if ((rc = voigt_grid(&nblocks))) return rc;
-  const long long nt = n_tiles_of(grid->n);
+  if ((rc = voigt_grid(&nblocks, on_nodes))) return rc;
+  const long long nt = n_tiles_of(n_grid);
   const long long nl = lines->n;
 
   if ((rc = cuda_check(cudaMemsetAsync(w.hdr, 0, sizeof(RoxWsHeader), s), "memset"))) return rc;
+  if (on_nodes &&
+      (rc = cuda_check(rox_launch_node_offsets(nodes->nu, nodes->n, nt * ROX_SPAN, w.node_d, w.span_base,
+                                               &w.hdr->status, ROX_EGRID, s),
+                       "node offsets kernel")))
+    return rc;
   if (nl > 0) {
-    if ((rc = cuda_check(rox_launch_windows(lines->nu0, nl, grid, cutoff, nullptr, nullptr, nullptr, nullptr, w.geo,
-                                            &w.hdr->evals_lines, &w.hdr->status, ROX_EUNSORTED, s),
-                         "windows kernel")))
-      return rc;
+    const cudaError_t we =
+        on_nodes ? rox_launch_node_windows(lines->nu0, nl, nodes->nu, nodes->n, cutoff, nullptr, nullptr, w.geo,
+                                           &w.hdr->evals_lines, &w.hdr->status, ROX_EUNSORTED, s)
+                 : rox_launch_windows(lines->nu0, nl, grid, cutoff, nullptr, nullptr, nullptr, nullptr, w.geo,
+                                      &w.hdr->evals_lines, &w.hdr->status, ROX_EUNSORTED, s);
+    if ((rc = cuda_check(we, "windows kernel"))) return rc;
     if ((rc = cuda_check(rox_launch_strengths_multi(lines, n_temps, temps.data(), qs.data(), Q_ref, w.S_T,
                                                     w.hdr->smax_bits, s),
                          "strengths kernel")))
@@ -344,21 +382,23 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
   L0.span_hi = w.thi;
   L0.gamma_ref = lines->gamma_ref;
   L0.n_t = lines->n_t;
-  L0.n_lattice = grid->n;
-  L0.dnu_f = (float)grid->dnu;
-  L0.nu_min_f = (float)grid->nu_min;
+  L0.node_d = w.node_d;
+  L0.span_base = w.span_base;
+  L0.n_lattice = n_grid;
+  L0.dnu_f = on_nodes ? 0.0f : (float)grid->dnu;
+  L0.nu_min_f = on_nodes ? 0.0f : (float)grid->nu_min;
   L0.width_f16 = lines->width_dtype == ROX_WIDTH_F16;
   L0.pad = 0;
   std::vector<RoxJobDev> jobs(n_pt);
   for (int k = 0; k < n_pt; k++) {
     RoxJobDev& J = jobs[k];
     J.S32 = w.S32 + (size_t)tidx[k] * (size_t)(nl > 0 ? nl : 1);
-    J.sigma = sigma_out + (size_t)k * (size_t)grid->n;
+    J.sigma = sigma_out + (size_t)k * (size_t)n_grid;
     J.smax_bits = &w.hdr->smax_bits[tidx[k]];
     J.l0 = 0;
     J.l1 = nl;
     J.first = 0;
-    J.n = grid->n;
+    J.n = n_grid;
     J.list = 0;
     J.span_first = 0;
     J.n_spans = (int32_t)nt;
@@ -368,9 +408,52 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
     J.flags = flags;
     J.pad = 0;
   }
-  if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, w.tail_part, w.tail_cnt, w.tail_cap, nblocks, s)))
+  if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, w.tail_part, w.tail_cnt, w.tail_cap, nblocks, s,
+                              on_nodes)))
     return rc;
   return ok();
+}
+}  // namespace
+
+extern "C" {
+
+int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const double* P_bar, const double* T,
+                   const double* Q_T, double Q_ref, double mass_amu, double cutoff, unsigned flags, float* sigma_out,
+                   void* ws, size_t ws_bytes, void* stream) {
+  int rc;
+  if ((rc = check_grid(grid))) return rc;
+  if ((rc = check_cutoff(cutoff, grid))) return rc;
+  return xsec_batch_impl(lines, grid, nullptr, n_pt, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, flags, sigma_out, ws,
+                         ws_bytes, stream);
+}
+
+size_t rox_xsec_nodes_workspace_size(int64_t n_lines, int64_t n_nodes, int n_temps) {
+  if (n_nodes <= 0 || n_lines < 0 || n_temps <= 0) return 0;
+  return ws_layout(nullptr, n_lines, n_nodes, n_temps, true).bytes;
+}
+
+int rox_xsec_nodes_batch(const rox_lines* lines, const rox_nodes* nodes, int n_pt, const double* P_bar,
+                         const double* T, const double* Q_T, double Q_ref, double mass_amu, double cutoff,
+                         unsigned flags, float* sigma_out, void* ws, size_t ws_bytes, void* stream) {
+  int rc;
+  if ((rc = check_nodes(nodes))) return rc;
+  if (!finite_pos(cutoff)) return fail(ROX_EINVAL, "cutoff must be > 0");
+  if (cutoff > 4000.0) return fail(ROX_ERANGE, "cutoff %g above 4000 cm^-1", cutoff);
+  return xsec_batch_impl(lines, nullptr, nodes, n_pt, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, flags, sigma_out, ws,
+                         ws_bytes, stream);
+}
+
+int rox_node_windows(const double* nu0_sorted, int64_t n_lines, const rox_nodes* nodes, double cutoff, int32_t* jlo,
+                     int32_t* jhi, void* stream) {
+  int rc;
+  if ((rc = check_nodes(nodes))) return rc;
+  if (!nu0_sorted || !jlo || !jhi) return fail(ROX_EINVAL, "nu0, jlo, jhi required");
+  if (n_lines < 0) return fail(ROX_EINVAL, "n_lines < 0");
+  if (!finite_pos(cutoff)) return fail(ROX_EINVAL, "cutoff must be > 0");
+  if (n_lines == 0) return ok();
+  return cuda_check(rox_launch_node_windows(nu0_sorted, n_lines, nodes->nu, nodes->n, cutoff, jlo, jhi, nullptr,
+                                            nullptr, nullptr, 0, (cudaStream_t)stream),
+                    "node windows kernel") ? ROX_ECUDA : ok();
 }
 
 int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double T, double Q_T, double Q_ref,
@@ -553,6 +636,8 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     L[l].span_hi = (const long long*)P.span_hi;
     L[l].gamma_ref = P.lines.gamma_ref;
     L[l].n_t = P.lines.n_t;
+    L[l].node_d = nullptr;
+    L[l].span_base = nullptr;
     L[l].n_lattice = P.lattice.n;
     L[l].dnu_f = (float)P.lattice.dnu;
     L[l].nu_min_f = (float)P.lattice.nu_min;

@@ -58,6 +58,71 @@ __global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, do
   }
 }
 
+// Windows on user-provided nodes (nu_k given, strictly increasing): the first node with
+// nu_k - nu0 >= -cutoff and the last with nu_k - nu0 <= cutoff, the differences rounded once
+// in double precision as the cutoff test is written; both are binary searches, the
+// difference being non-decreasing in k. The line centre is carried as a double-float pair
+// {hi, lo} (float hi = nu0 rounded, lo = the remainder) in the geometry record.
+__global__ void k_node_windows(const double* __restrict__ nu0s, long long n_lines, const double* __restrict__ nodes,
+                               long long n, double cutoff, int32_t* jlo_out, int32_t* jhi_out, float4* geo_out,
+                               unsigned long long* evals_out, int32_t* unsorted_out, int32_t unsorted_value) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long ev = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_lines; i += stride) {
+    const double nu0 = nu0s[i];
+    if (i > 0 && nu0s[i - 1] > nu0 && unsorted_out) *unsorted_out = unsorted_value;
+    long long a = 0, b = n;
+    while (a < b) {
+      const long long mid = (a + b) >> 1;
+      if (__dsub_rn(nodes[mid], nu0) >= -cutoff) b = mid; else a = mid + 1;
+    }
+    const long long jl = a;
+    b = n;
+    while (a < b) {
+      const long long mid = (a + b) >> 1;
+      if (__dsub_rn(nodes[mid], nu0) > cutoff) b = mid; else a = mid + 1;
+    }
+    const long long jh = a - 1;
+    if (jh >= jl) ev += (unsigned long long)(jh - jl + 1);
+    if (jlo_out) jlo_out[i] = (int32_t)jl;
+    if (jhi_out) jhi_out[i] = (int32_t)jh;
+    if (geo_out) {
+      const float hi = (float)nu0;
+      geo_out[i] = make_float4(hi, (float)(nu0 - (double)hi), __int_as_float((int)jl), __int_as_float((int)jh));
+    }
+  }
+  if (evals_out) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evals_out, ev);
+  }
+}
+
+// Per node, its offset from the first node of its ROX_SPAN-node span as a double-float pair
+// {hi, lo}; per span, that first node as a pair. The node array is padded to whole spans with
+// nodes continuing the last spacing (computed, never written out). Nodes that are not finite
+// or not strictly increasing set *status = bad_value.
+__global__ void k_node_offsets(const double* __restrict__ nodes, long long n, long long n_pad, float2* d_out,
+                               float2* base_out, int32_t* status, int32_t bad_value) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  const double last = nodes[n - 1];
+  double step = n > 1 ? last - nodes[n - 2] : 1.0;
+  if (!(step > 0.0)) step = 1.0;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n_pad; j += stride) {
+    const long long s = j / ROX_SPAN;
+    const double base = nodes[s * ROX_SPAN];
+    const double v = j < n ? nodes[j] : last + (double)(j - n + 1) * step;
+    const double d = v - base;
+    const float dh = (float)d;
+    d_out[j] = make_float2(dh, (float)(d - (double)dh));
+    if (j == s * ROX_SPAN) {
+      const float bh = (float)base;
+      base_out[s] = make_float2(bh, (float)(base - (double)bh));
+    }
+    if (j < n && (!isfinite(v) || (j > 0 && !(v > nodes[j - 1])))) *status = bad_value;
+  }
+}
+
 // Tile t meets line i iff jhi_i >= t*W and jlo_i <= (t+1)*W - 1. Both bounds are
 // non-decreasing along the sorted list, so lo[t] = first i with jhi_i >= t*W and
 // hi[t] = first i with jlo_i >= (t+1)*W. Each line writes the boundaries between its
@@ -143,6 +208,21 @@ cudaError_t rox_launch_windows(const double* nu0, long long n_lines, const rox_g
                                cudaStream_t s) {
   k_windows<<<grid_for(n_lines), 256, 0, s>>>(nu0, n_lines, g->nu_min, g->dnu, 1.0 / g->dnu, g->n, cutoff, jlo, jhi, k0,
                                                f, geo, evals, unsorted, unsorted_value);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_node_windows(const double* nu0, long long n_lines, const double* nodes, long long n,
+                                    double cutoff, int32_t* jlo, int32_t* jhi, float4* geo,
+                                    unsigned long long* evals, int32_t* unsorted, int32_t unsorted_value,
+                                    cudaStream_t s) {
+  k_node_windows<<<grid_for(n_lines), 256, 0, s>>>(nu0, n_lines, nodes, n, cutoff, jlo, jhi, geo, evals, unsorted,
+                                                   unsorted_value);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_node_offsets(const double* nodes, long long n, long long n_pad, float2* d, float2* base,
+                                    int32_t* status, int32_t bad_value, cudaStream_t s) {
+  k_node_offsets<<<grid_for(n_pad), 256, 0, s>>>(nodes, n, n_pad, d, base, status, bad_value);
   return cudaGetLastError();
 }
 

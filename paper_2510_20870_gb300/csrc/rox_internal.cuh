@@ -54,6 +54,11 @@ struct RoxListDev {
   const long long* span_hi;   //   and one past the last
   const void* gamma_ref;
   const void* n_t;
+  // user-provided nodes only (NULL on a uniform grid): per node its offset from the first node
+  // of its span, per span that first node, both as double-float pairs {hi, lo}; geo then holds
+  // {nu0 hi, nu0 lo, jlo, jhi}
+  const float2* node_d;
+  const float2* span_base;
   long long n_lattice;
   float dnu_f;
   float nu_min_f;

@@ -83,10 +83,25 @@ __device__ __forceinline__ float masked_far(float X, const float4& a, const floa
   return n * rox_rcp(d);
 }
 
+// X = nu - nu0 at this lane's point of sub-span m. Uniform grid: X0 + 32 m dnu, X0 the offset
+// at the lane's first point (from the exact index decomposition). User-provided nodes: the
+// node's double-float offset from the span's first node, D[32 m] = {hi, lo}, minus the line's,
+// a = {c hi, c lo}; the hi parts cancel exactly near the line, so X keeps its relative accuracy.
+template <bool NU>
+__device__ __forceinline__ float pos(int m, float X0, const float4& a, const float2* D, float dnu_f) {
+  if constexpr (NU) {
+    const float2 d = D[32 * m];
+    return (d.x - a.x) + (d.y - a.y);
+  } else {
+    return fmaf((float)(32 * m), dnu_f, X0);
+  }
+}
+
 // Pass 1 for a line whose window edge falls inside the span: per 32-point sub-span, skipped if
 // outside the window, the masked far formula otherwise, masked per point where cut.
+template <bool NU>
 __device__ __forceinline__ void edge_line(const float4& a, const float4& b, const float4& c, int Aw, int lane,
-                                          float Jf, float dnu_f, float (&acc)[ROX_K]) {
+                                          float Jf, float dnu_f, const float2* D, float (&acc)[ROX_K]) {
   const float X0 = fmaf(Jf - a.x, dnu_f, -a.y);
   const int jlo = __float_as_int(c.x), jhi = __float_as_int(c.y);
 #pragma unroll
@@ -94,7 +109,7 @@ __device__ __forceinline__ void edge_line(const float4& a, const float4& b, cons
     const int am = Aw + 32 * m, bm = am + 31;
     if (bm < jlo || am > jhi) continue;
     const int j = am + lane;
-    const float v = masked_far(fmaf((float)(32 * m), dnu_f, X0), a, b);
+    const float v = masked_far(pos<NU>(m, X0, a, D, dnu_f), a, b);
     acc[m] += (j >= jlo && j <= jhi) ? v : 0.0f;
   }
 }
@@ -104,8 +119,9 @@ __device__ __forceinline__ void edge_line(const float4& a, const float4& b, cons
 // takes line i iff it lies in the window, m in [ceil((jlo-Aw-lane)/32), floor((jhi-Aw-lane)/32)]
 // (the exact integer window), and outside the slow zone. Lines arrive sorted by nu0, so
 // paired edge lines have their edges in the same or a neighbouring sub-span.
+template <bool NU>
 __device__ __forceinline__ void edge_pair(const Rec& r0, const Rec& r1, int Aw, int lane, float Jf, float dnu_f,
-                                          float (&acc)[ROX_K]) {
+                                          const float2* D, float (&acc)[ROX_K]) {
   const float4 a0 = r0.a, b0 = r0.b, a1 = r1.a, b1 = r1.b;
   const int lo0 = __float_as_int(r0.c.x) - Aw, hi0 = __float_as_int(r0.c.y) - Aw;
   const int lo1 = __float_as_int(r1.c.x) - Aw, hi1 = __float_as_int(r1.c.y) - Aw;
@@ -120,7 +136,7 @@ __device__ __forceinline__ void edge_pair(const Rec& r0, const Rec& r1, int Aw, 
 #pragma unroll
   for (int m = 0; m < ROX_K; m++) {
     if (m < mf || m > ml) continue;
-    const float x0 = fmaf((float)(32 * m), dnu_f, X0), x1 = fmaf((float)(32 * m), dnu_f, X1);
+    const float x0 = pos<NU>(m, X0, a0, D, dnu_f), x1 = pos<NU>(m, X1, a1, D, dnu_f);
     const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
     if (m >= cf && m <= cl) {
       const float d0 = fmaf(t0, t0, a0.w), d1 = fmaf(t1, t1, a1.w);
@@ -144,8 +160,9 @@ __device__ __forceinline__ void edge_pair(const Rec& r0, const Rec& r1, int Aw, 
 // 5-level one if |z| >= 6 there (both only get more accurate further out), else rox_re_w
 // per point. Accumulated into the warp's shared-memory row zacc[32 m + lane] (each lane
 // touches only its own points).
+template <bool NU>
 __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float Jf, float dnu_f, const float* daw,
-                                          float* zacc) {
+                                          const float2* D, float* zacc) {
   const float X0 = fmaf(Jf - rq.a.x, dnu_f, -rq.a.y);
   const int jlo = __float_as_int(rq.c.x), jhi = __float_as_int(rq.c.y);
   const int zlo = __float_as_int(rq.c.z), zhi = __float_as_int(rq.c.w);
@@ -155,27 +172,34 @@ __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float
   if (rq.d.w != 0.0f) {
     for (int m = (lo - Aw) >> 5; m <= ((hi - Aw) >> 5); m++) {
       const int j = Aw + 32 * m + lane;
-      const float Xm = fmaf((float)(32 * m), dnu_f, X0);
+      const float Xm = pos<NU>(m, X0, rq.a, D, dnu_f);
       const float t = fmaf(Xm, Xm, rq.a.z);
       if (!(t < rq.b.w) || j < jlo || j > jhi) continue;
-      const float X = fmaf((float)j - rq.a.x, dnu_f, -rq.a.y);
+      // the uniform grid recomputes X from the index in one rounding; node offsets are exact already
+      const float X = NU ? Xm : fmaf((float)j - rq.a.x, dnu_f, -rq.a.y);
       zacc[32 * m + lane] += pcore * rox_re_w_core(daw, fabsf(X) * invG, y);
     }
     return;
   }
-  const float centre = rq.a.x + rq.a.y / dnu_f;     // k0 + f, within 0.25 grid steps
+  const float centre = rq.a.x + rq.a.y / dnu_f;     // k0 + f, within 0.25 grid steps (uniform grid)
   const float y2 = y * y;
   for (int m = (lo - Aw) >> 5; m <= ((hi - Aw) >> 5); m++) {
     const int am = Aw + 32 * m, bm = am + 31;
     const int j = am + lane;
-    const float Xm = fmaf((float)(32 * m), dnu_f, X0);
+    const float Xm = pos<NU>(m, X0, rq.a, D, dnu_f);
     const float t = fmaf(Xm, Xm, rq.a.z);
+    float xm;   // |X| of the sub-span's point nearest the line centre, in units of gamma_G
+    if constexpr (NU) {
+      const float Xa = __shfl_sync(0xffffffffu, Xm, 0), Xb = __shfl_sync(0xffffffffu, Xm, 31);
+      xm = (Xa <= 0.0f && Xb >= 0.0f ? 0.0f : fminf(fabsf(Xa), fabsf(Xb))) * invG;
+    } else {
+      const float dc = (centre >= (float)am && centre <= (float)bm)
+                           ? 0.0f : fminf(fabsf((float)am - centre), fabsf((float)bm - centre));
+      xm = fmaxf(dc - 1.0f, 0.0f) * dnu_f * invG;
+    }
     if (!(t < rq.b.w) || j < jlo || j > jhi) continue;
-    const float dc = (centre >= (float)am && centre <= (float)bm)
-                         ? 0.0f : fminf(fabsf((float)am - centre), fabsf((float)bm - centre));
-    const float xm = fmaxf(dc - 1.0f, 0.0f) * dnu_f * invG;
     const float sm = fmaf(xm, xm, y2);
-    const float X = fmaf((float)j - rq.a.x, dnu_f, -rq.a.y);
+    const float X = NU ? Xm : fmaf((float)j - rq.a.x, dnu_f, -rq.a.y);
     const float x = fabsf(X) * invG;
     float r;
     if (sm >= ROX_S_CF3) r = rox_re_w_cf3(x, y);
@@ -185,7 +209,11 @@ __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float
   }
 }
 
+// NU: the lists are on user-provided nodes (node offsets in dynamic shared memory, one
+// ROX_SPAN row of float2 per warp).
+template <bool NU>
 __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant__ RoxVoigtArgs A) {
+  extern __shared__ float2 s_nodes[];
   __shared__ float4 s_geo[ROX_WARPS][2][32];
   __shared__ float s_S[ROX_WARPS][2][32];
   __shared__ Rec s_rec[ROX_WARPS][32];
@@ -206,6 +234,8 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
   Rec* rec = s_rec[w];
   float* zacc = s_zacc[w];
   float* stot = s_tot[w];
+  float2* Drow = NU ? s_nodes + w * ROX_SPAN : nullptr;   // this span's node offsets
+  const float2* D = NU ? Drow + lane : nullptr;
   unsigned long long evals = 0;   // (line, point) pairs inside the cutoff and the job's window
 
   for (;;) {
@@ -232,11 +262,22 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
     const int span = J.span_first + J.n_spans - 1 - local;       // wide-line (high nu) spans first
     const int f16 = Lst.width_f16;
     const float dnu_f = Lst.dnu_f;
-    const float margin_cm = ROX_FAST_MARGIN * 32.0f * (ROX_K - 1) * dnu_f;
+    // offsets on a uniform grid round once more (X0 + 32 m dnu), hence the precision margin
+    const float margin_cm = NU ? 0.0f : ROX_FAST_MARGIN * 32.0f * (ROX_K - 1) * dnu_f;
     const int Aw = span * ROX_SPAN;
     const int Bw = Aw + ROX_SPAN - 1;
     const float Jf = (float)(Aw + lane);
     if (*Lst.status != ROX_OK) continue;           // list not prepared from sorted lines
+    float bh = 0.f, bl = 0.f, Ws = 0.f;             // span's first node; offset of its last node
+    if constexpr (NU) {
+#pragma unroll
+      for (int m = 0; m < ROX_K; m++) Drow[32 * m + lane] = Lst.node_d[(long long)Aw + 32 * m + lane];
+      const float2 b = Lst.span_base[span];
+      bh = b.x;
+      bl = b.y;
+      __syncwarp();
+      Ws = Drow[ROX_SPAN - 1].x;
+    }
     const long long lo = max(Lst.span_lo[span], J.l0), hi = min(Lst.span_hi[span], J.l1);
     const long long wlo = J.first > Aw ? J.first : Aw;             // evaluated points of this span
     const long long whi = (J.first + J.n - 1) < Bw ? (J.first + J.n - 1) : Bw;
@@ -282,8 +323,18 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
           const float4 g = geo_st[buf][lane];
           const float Sp = S_st[buf][lane];
           const int jlo = __float_as_int(g.z), jhi = __float_as_int(g.w);
-          const int k0 = (int)g.x;
-          const float nu0f = Lst.nu_min_f + fmaf(g.x, dnu_f, g.y);
+          float nu0f, ax, ay;   // line centre; its offset state {k0, f dnu} or {c hi, c lo}
+          if constexpr (NU) {
+            // c = nu0 - (span's first node) as a double-float pair (the hi parts cancel exactly)
+            nu0f = g.x;
+            const float ch = g.x - bh, cl = g.y - bl;
+            ax = ch + cl;
+            ay = cl - (ax - ch);
+          } else {
+            nu0f = Lst.nu_min_f + fmaf(g.x, dnu_f, g.y);
+            ax = g.x;
+            ay = g.y;
+          }
           const float gG = nu0f * J.gG_fac;
           const float gL = gref * exp2f(nt * J.l2_ratio) * J.p_fac;
           const long long ov = min((long long)jhi, whi) - max((long long)jlo, wlo) + 1;
@@ -298,14 +349,25 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
           // zone |z| < 6.5 not widened by the margin: the core forms cover all of it
           const bool core_only = fc.r2 == ROX_S_PADE && hz >= margin_cm;
           hz = fmaxf(hz, margin_cm);
-          const float hzg = fminf(hz / dnu_f * 1.0001f, 8.0e6f);
-          const float f = g.y / dnu_f;
-          const int zlo = k0 + (int)floorf(f - hzg) - 1;
-          const int zhi = k0 + (int)ceilf(f + hzg) + 1;
+          int zlo, zhi;
+          bool zoned;
+          if constexpr (NU) {
+            // the span's offsets run from -c to Ws - c; pass 2 then scans the window itself
+            const float hzp = hz * 1.001f + 1e-6f * (fabsf(ax) + Ws);
+            zoned = -ax < hzp && Ws - ax > -hzp;
+            zlo = jlo;
+            zhi = jhi;
+          } else {
+            const int k0 = (int)g.x;
+            const float hzg = fminf(hz / dnu_f * 1.0001f, 8.0e6f);
+            const float f = g.y / dnu_f;
+            zlo = k0 + (int)floorf(f - hzg) - 1;
+            zhi = k0 + (int)ceilf(f + hzg) + 1;
+            zoned = !(Bw < zlo || Aw > zhi);
+          }
           const bool covers = Aw >= jlo && Bw <= jhi;
-          const bool zoned = !(Bw < zlo || Aw > zhi);
           const float vg = fc.alpha * gG2;
-          r.a = make_float4(g.x, g.y, vg, fc.beta * (gG2 * gG2));
+          r.a = make_float4(ax, ay, vg, fc.beta * (gG2 * gG2));
           r.b = make_float4(pY, pY * (fc.kappa * gG2), __uint_as_float((covers ? 1u : 0u) | (zoned ? 2u : 0u)),
                             fmaf(hz, hz, vg));
           r.c = make_float4(g.z, g.w, __int_as_float(zlo), __int_as_float(zhi));
@@ -342,8 +404,8 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
 #pragma unroll
             for (int m = 0; m < ROX_K; m++) {
-              const float x0 = fmaf((float)(32 * m), dnu_f, X0);
-              const float x1 = fmaf((float)(32 * m), dnu_f, X1);
+              const float x0 = pos<NU>(m, X0, a0, D, dnu_f);
+              const float x1 = pos<NU>(m, X1, a1, D, dnu_f);
               const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
               const float d0 = fmaf(t0, t0, a0.w), d1 = fmaf(t1, t1, a1.w);
               const float n0 = fmaf(t0, b0v.x, b0v.y), n1 = fmaf(t1, b1v.x, b1v.y);
@@ -353,7 +415,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             }
           } else {
 #pragma unroll
-            for (int m = 0; m < ROX_K; m++) acc[m] += far_term(fmaf((float)(32 * m), dnu_f, X0), a0, b0v);
+            for (int m = 0; m < ROX_K; m++) acc[m] += far_term(pos<NU>(m, X0, a0, D, dnu_f), a0, b0v);
           }
         }
         while (zmask) {
@@ -368,8 +430,8 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
 #pragma unroll
             for (int m = 0; m < ROX_K; m++) {
-              const float x0 = fmaf((float)(32 * m), dnu_f, X0);
-              const float x1 = fmaf((float)(32 * m), dnu_f, X1);
+              const float x0 = pos<NU>(m, X0, a0, D, dnu_f);
+              const float x1 = pos<NU>(m, X1, a1, D, dnu_f);
               const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
               const bool f0 = t0 >= b0v.w, f1 = t1 >= b1v.w;   // outside the slow zone
               const float d0 = f0 ? fmaf(t0, t0, a0.w) : 1.0f, d1 = f1 ? fmaf(t1, t1, a1.w) : 1.0f;
@@ -381,24 +443,24 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             }
           } else {
 #pragma unroll
-            for (int m = 0; m < ROX_K; m++) acc[m] += masked_far(fmaf((float)(32 * m), dnu_f, X0), a0, b0v);
+            for (int m = 0; m < ROX_K; m++) acc[m] += masked_far(pos<NU>(m, X0, a0, D, dnu_f), a0, b0v);
           }
         }
         for (unsigned em = emask; em;) {
           const int i0 = __ffs(em) - 1;
           em &= em - 1;
           if (!em) {
-            edge_line(rec[i0].a, rec[i0].b, rec[i0].c, Aw, lane, Jf, dnu_f, acc);
+            edge_line<NU>(rec[i0].a, rec[i0].b, rec[i0].c, Aw, lane, Jf, dnu_f, D, acc);
             break;
           }
           const int i1 = __ffs(em) - 1;
           em &= em - 1;
-          edge_pair(rec[i0], rec[i1], Aw, lane, Jf, dnu_f, acc);
+          edge_pair<NU>(rec[i0], rec[i1], Aw, lane, Jf, dnu_f, D, acc);
         }
         // ---- pass 2: the points each zoned line left out of pass 1, full Faddeeva forms
         for (unsigned pm = pmask; pm; pm &= pm - 1) {
           const Rec rq = rec[__ffs(pm) - 1];
-          zone_line(rq, Aw, lane, Jf, dnu_f, s_daw, zacc);
+          zone_line<NU>(rq, Aw, lane, Jf, dnu_f, s_daw, D, zacc);
         }
         __syncwarp();
         // compensated (Kahan) accumulation of the partial sums, every 4 batches
@@ -476,13 +538,29 @@ __global__ void k_faddeeva(const float* x, const float* y, float* out, long long
 
 }  // namespace
 
-cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, cudaStream_t s) {
-  k_voigt<<<n_blocks, ROX_THREADS, 0, s>>>(A);
+#define ROX_NODES_SMEM (ROX_WARPS * ROX_SPAN * sizeof(float2))
+
+cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, cudaStream_t s) {
+  if (nodes) {
+    // static shared memory plus the node rows exceed 48 KB: opt in (idempotent, per device)
+    cudaError_t e = cudaFuncSetAttribute(k_voigt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ROX_NODES_SMEM);
+    if (e != cudaSuccess) return e;
+    k_voigt<true><<<n_blocks, ROX_THREADS, ROX_NODES_SMEM, s>>>(A);
+  } else {
+    k_voigt<false><<<n_blocks, ROX_THREADS, 0, s>>>(A);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t rox_voigt_blocks_per_sm(int* nb) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt, ROX_THREADS, 0);
+cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes) {
+  if (nodes) {
+    cudaError_t e = cudaFuncSetAttribute(k_voigt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ROX_NODES_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<true>, ROX_THREADS, ROX_NODES_SMEM);
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<false>, ROX_THREADS, 0);
 }
 
 cudaError_t rox_launch_faddeeva(const float* x, const float* y, float* out, long long n, cudaStream_t s) {

@@ -13,8 +13,9 @@ list can be regenerated on its own, which is how the oracle checks a sample of
 a line list too large for it.
 """
 from .philox import philox4x32_10, uniform01
-from .workloads import (CONFIGS, SERVE_LISTS, Workload, make_lines, make_lines_at, nu0_in_chunks, q_table,
-                        grid_of, pt_points, serve_requests)
+from .workloads import (CONFIGS, FIXED_R, SERVE_LISTS, Workload, fixed_resolution_grid, grid_of, irregular_nodes,
+                        make_lines, make_lines_at, nu0_in_chunks, pt_points, q_table, serve_requests)
 
 __all__ = ["philox4x32_10", "uniform01", "CONFIGS", "SERVE_LISTS", "Workload", "make_lines", "make_lines_at",
-           "nu0_in_chunks", "q_table", "grid_of", "pt_points", "serve_requests"]
+           "nu0_in_chunks", "q_table", "grid_of", "pt_points", "serve_requests", "FIXED_R", "fixed_resolution_grid",
+           "irregular_nodes"]

@@ -200,3 +200,29 @@ def serve_requests(rate_per_s: float, count: int, seed: int = 5):
                             float(math.exp(math.log(1e-5) + (math.log(1e2) - math.log(1e-5)) * u_p[i])),
                             float(300.0 + 2700.0 * u_t[i]), 300.0 + 0.01 * k0, n))
     return reqs
+
+
+# User-provided grids (NEXT-1): constant resolving power, and irregular spacing
+FIXED_R = 645_000.0        # over 300-30000 cm^-1: 2,970,338 nodes, about the size of config 2's grid
+
+
+def fixed_resolution_grid(nu_lo: float, nu_hi: float, R: float):
+    """Nodes of constant resolving power R = lambda/dlambda: nu_k = nu_lo * (1 + 1/R)^k for
+    k = 0..K, K the largest index keeping nu_k <= nu_hi (float64, strictly increasing)."""
+    q = 1.0 + 1.0 / float(R)
+    K = int(np.floor(np.log(float(nu_hi) / float(nu_lo)) / np.log(q)))
+    while K >= 0 and nu_lo * q ** K > nu_hi:
+        K -= 1
+    return float(nu_lo) * np.power(q, np.arange(K + 1, dtype=np.float64))
+
+
+def irregular_nodes(seed: int, lo: float, hi: float, n: int):
+    """n strictly increasing nodes in [lo, hi] with uneven spacing: half uniform at random,
+    half in a few tight clusters (Philox stream 40 of `seed`)."""
+    u = uniform01(seed, 40, 0, 2 * n)
+    base = lo + (hi - lo) * u[:n // 2]
+    centres = lo + (hi - lo) * u[n // 2:n // 2 + 8]
+    width = 1e-3 * (hi - lo)
+    clus = centres[(np.arange(n - n // 2) % 8)] + width * (u[n:n + n - n // 2] - 0.5)
+    nodes = np.unique(np.clip(np.concatenate([base, clus]), lo, hi))
+    return nodes.astype(np.float64)
