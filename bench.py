@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--lines", type=int, default=None,
                     help="use only the first N lines of the workload (smaller profiling case)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (request-latency) leg")
+    ap.add_argument("--nodes", action="store_true",
+                    help="user-provided grid: the workload's lines on nodes of fixed resolving power R = %g over the "
+                         "same wavenumber range (rox_xsec_nodes_batch)" % rs.FIXED_R)
     ap.add_argument("--serve-rates", default="50,100", help="Poisson request rates (req/s) of the serving leg")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="arrival window per rate (s)")
     return ap.parse_args()
@@ -83,6 +86,10 @@ def q_oracle(q, T):
 def _oracle_window(args):
     sub, grid, j0, j1, P, T, Qt, Qr, mass, cutoff = args
     import oracle
+    if isinstance(grid, np.ndarray):           # user-provided nodes: grid holds the window's nodes
+        s = oracle.xsec_nodes(sub, grid, P, T, Qt, Qr, mass, cutoff)
+        jlo, jhi = oracle.node_windows(sub["nu0"], grid, cutoff)
+        return int(np.sum(np.maximum(jhi - jlo + 1, 0))), float(s.sum())
     s = oracle.xsec_window(sub, grid, j0, j1, P, T, Qt, Qr, mass, cutoff)
     jlo, jhi = oracle.window_indices(sub["nu0"], *grid, cutoff)
     ev = int(np.sum(np.maximum(np.minimum(jhi, j1 - 1) - np.maximum(jlo, j0) + 1, 0)))
@@ -93,12 +100,18 @@ def oracle_sample_tasks(Ls, grid, P, T, Qt, Qr, mass, cutoff, n_windows, width, 
     rng = np.random.default_rng(seed)
     tasks = []
     nu0 = Ls["nu0"]
-    for s in rng.integers(0, grid[2] - width, n_windows):
-        lo = grid[0] + grid[1] * s - cutoff - 1.0
-        hi = grid[0] + grid[1] * (s + width) + cutoff + 1.0
+    nodes = isinstance(grid, np.ndarray)
+    n = grid.size if nodes else grid[2]
+    for s in rng.integers(0, n - width, n_windows):
+        if nodes:
+            lo, hi = grid[s] - cutoff - 1.0, grid[s + width - 1] + cutoff + 1.0
+        else:
+            lo = grid[0] + grid[1] * s - cutoff - 1.0
+            hi = grid[0] + grid[1] * (s + width) + cutoff + 1.0
         a, b = np.searchsorted(nu0, lo), np.searchsorted(nu0, hi)
         sub = {k: (v[a:b] if isinstance(v, np.ndarray) else v) for k, v in Ls.items()}
-        tasks.append((sub, grid, int(s), int(s) + width, P, T, Qt, Qr, mass, cutoff))
+        g = grid[s:s + width].copy() if nodes else grid
+        tasks.append((sub, g, int(s), int(s) + width, P, T, Qt, Qr, mass, cutoff))
     return tasks
 
 
@@ -129,8 +142,9 @@ def cpu_baseline(w, grid, P, T, q, Ls, target_s):
     tasks = oracle_sample_tasks(Ls, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, n_win, width, 8)
     ev, dt = time_oracle(tasks, cores)
     return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d random windows of %d grid points of the %s workload (all lines within the cutoff "
-                      "of each window), FP64 scipy.special.wofz, %d evals in %.1f s" % (n_win, width, w.name, ev, dt)}
+            "sample": "%d random windows of %d %s of the %s workload (all lines within the cutoff "
+                      "of each window), FP64 scipy.special.wofz, %d evals in %.1f s" % (
+                          n_win, width, "nodes" if isinstance(grid, np.ndarray) else "grid points", w.name, ev, dt)}
 
 
 def run_reference(args):
@@ -288,18 +302,33 @@ def run_gpu(args):
     n = len(host["nu0"])
     h2d_bytes = sum(v.numel() * v.element_size() for v in pinned.values())
     sort_ws = torch.empty(rox.rox_sort_workspace_size(n), dtype=torch.uint8, device=dev)
-    ws = torch.empty(rox.rox_xsec_workspace_size(n, grid, 1), dtype=torch.uint8, device=dev)
-    sigma = torch.empty((1, grid[2]), dtype=torch.float32, device=dev)
-    sigma_host = torch.empty((1, grid[2]), dtype=torch.float32).pin_memory()
+    if args.nodes:
+        nodes_np = rs.fixed_resolution_grid(w.grid_lo, w.grid_hi, rs.FIXED_R)
+        nodes_pin = torch.from_numpy(nodes_np).pin_memory()
+        nodes_dev = torch.empty_like(nodes_pin, device=dev)
+        nodes_dev.copy_(nodes_pin)
+        n_grid = nodes_np.size
+        h2d_bytes += n_grid * 8
+        ws = torch.empty(rox.rox_xsec_nodes_workspace_size(n, n_grid, 1), dtype=torch.uint8, device=dev)
+    else:
+        n_grid = grid[2]
+        ws = torch.empty(rox.rox_xsec_workspace_size(n, grid, 1), dtype=torch.uint8, device=dev)
+    sigma = torch.empty((1, n_grid), dtype=torch.float32, device=dev)
+    sigma_host = torch.empty((1, n_grid), dtype=torch.float32).pin_memory()
     stream = torch.cuda.current_stream()
 
     def upload_and_sort():
         for k, v in pinned.items():
             raw[k].copy_(v, non_blocking=True)
+        if args.nodes:
+            nodes_dev.copy_(nodes_pin, non_blocking=True)
         rox.rox_sort_lines(raw, lines, None, sort_ws)
 
     def step():
-        rox.rox_xsec(lines, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
+        if args.nodes:
+            rox.rox_xsec_nodes_batch(lines, nodes_dev, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws)
+        else:
+            rox.rox_xsec(lines, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
 
     upload_and_sort()
     step()
@@ -361,7 +390,8 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_ms = float(tt.item())
     e2e_value = world * evals * e2e_steps / (e2e_ms * 1e-3) if e2e_steps else None
-    assert np.isfinite(sigma_host.numpy()).all()
+    if e2e_steps:
+        assert np.isfinite(sigma_host.numpy()).all()
 
     csum = clocks.summary()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -369,7 +399,7 @@ def run_gpu(args):
     v_ms = statistics.mean(voigt_ms)
     achieved = evals * FLOPS_PER_EVAL / (v_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": VOIGT_TRAFFIC_BYTES if (args.config == 2 and args.lines is None) else None,
+            "traffic": VOIGT_TRAFFIC_BYTES if (args.config == 2 and args.lines is None and not args.nodes) else None,
             "traffic_note": "ncu capture of the 2e6-line case scaled by evaluations", "kernel": "k_voigt",
             "kernel_ms": v_ms,
             "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, SM_MAX_MHZ),
@@ -389,17 +419,23 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         Ls = oracle.sort_lines(host)
-        cpu = cpu_baseline(w, grid, P, T, q, Ls, args.cpu_seconds)
+        cpu = cpu_baseline(w, nodes_np if args.nodes else grid, P, T, q, Ls, args.cpu_seconds)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "%s: %d lines (%s-style), grid %g-%g cm^-1 at %g (%d points), cutoff %g "
-                           "cm^-1, (P,T)=(%g bar, %g K)" % (w.name, n, "ExoMol" if w.convention == 1 else "HITRAN", w.grid_lo, w.grid_hi, w.dnu, grid[2],
-                                                           w.cutoff, P, T),
+                "config": {"workload": (("%s: %d lines (%s-style), grid %g-%g cm^-1 at %g (%d points), cutoff %g "
+                                         "cm^-1, (P,T)=(%g bar, %g K)") % (
+                                             w.name, n, "ExoMol" if w.convention == 1 else "HITRAN", w.grid_lo, w.grid_hi,
+                                             w.dnu, grid[2], w.cutoff, P, T)) if not args.nodes else (
+                                   ("%s lines on user-provided nodes: %d lines (%s-style), fixed resolving power "
+                                    "R = %g over %g-%g cm^-1 (%d nodes), cutoff %g cm^-1, (P,T)=(%g bar, %g K)") % (
+                                       w.name, n, "ExoMol" if w.convention == 1 else "HITRAN", rs.FIXED_R, w.grid_lo,
+                                       w.grid_hi, n_grid, w.cutoff, P, T)),
                            "evals_per_step": evals, "xsecs_per_s": world * args.steps / (ms * 1e-3),
-                           "step": "rox_xsec on the resident nu0-sorted list (strengths, widths, windows, tile "
+                           "step": ("rox_xsec_nodes_batch" if args.nodes else "rox_xsec") +
+                                   " on the resident nu0-sorted list (strengths, widths, windows, tile "
                                    "ranges, Voigt accumulate); the once-per-list sort is inside e2e",
                            "l2": "inputs larger than L2 (line list %.0f MB, workspace %.0f MB)" % (
                                h2d_bytes / 1e6, ws_mb),
@@ -408,9 +444,11 @@ def run_gpu(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
                         "d2h_bytes_per_step": sigma_bytes,
                         "ms_per_step": e2e_ms / e2e_steps if e2e_steps else None,
-                        "includes": "H2D of the unsorted list, rox_sort_lines, rox_xsec, D2H of sigma"},
-                "gpu_launches": args.steps * 4,
-                "gpu_launches_note": "per step: windows, strengths, tile ranges, Voigt kernels (+1 memset)",
+                        "includes": "H2D of the unsorted list%s, rox_sort_lines, %s, D2H of sigma" % (
+                            " and the nodes" if args.nodes else "", "rox_xsec_nodes_batch" if args.nodes else "rox_xsec")},
+                "gpu_launches": args.steps * (6 if args.nodes else 5),
+                "gpu_launches_note": "per step: %swindows, strengths, strength scaling, tile ranges, Voigt kernels "
+                                     "(+ memsets)" % ("node offsets, " if args.nodes else ""),
                 "clocks": csum}
         print(json.dumps(line))
     if dist is not None:
