@@ -297,13 +297,43 @@ def pin_fixed_resolution(o):
     assert nodes.size == int(math.floor(math.log(2500.0 / 2000.0) / math.log1p(1.0 / R))) + 1
 
 
+# ---------------------------------------------------------------- main-contributor selection (R15)
+def pin_select_rules(o):
+    rng = np.random.default_rng(13)
+    nu0 = np.sort(rng.uniform(1000.0, 1100.0, 4000))
+    S = 10.0 ** rng.uniform(-30, -18, nu0.size)
+    assert o.select_mask(nu0, S, 0.0, 1.0).all()                     # rel = 0 keeps every line
+    one = o.select_mask(nu0, S, 1.0, 1e9)                              # one bin, rel = 1: the strongest only
+    assert one.sum() == 1 and S[one][0] == S.max()
+    m = o.select_mask(nu0, S, 1e-3, 1.0)
+    b = np.floor((nu0 - nu0[0]) / 1.0).astype(int)
+    for k in np.unique(b):                                             # brute force per bin
+        sel = b == k
+        assert np.array_equal(m[sel], S[sel] >= 1e-3 * S[sel].max())
+    assert o.select_mask(nu0, S, 1e-2, 1.0).sum() <= m.sum() <= o.select_mask(nu0, S, 1e-4, 1.0).sum()
+
+
+def pin_select_sum(o):
+    # selection with rel = 0 is the full sum bit for bit; otherwise it is the full sum of the kept lines
+    L = _small(n=60)
+    P, T, Qt, Qr, mass, cut = ARGS
+    full = o.xsec_windowed(L, GRID, *ARGS)
+    L0, keep0 = o.select_lines(L, T, Qt, Qr, 0.0, 1.0)
+    assert keep0.all() and np.array_equal(o.xsec_windowed(L0, GRID, *ARGS), full)
+    Lk, keep = o.select_lines(L, T, Qt, Qr, 1e-3, 5.0)
+    assert 0 < keep.sum() < keep.size
+    drop = {k: (v[~keep] if isinstance(v, np.ndarray) else v) for k, v in L.items()}
+    assert np.allclose(o.xsec_windowed(Lk, GRID, *ARGS) + o.xsec_windowed(drop, GRID, *ARGS), full,
+                       rtol=1e-13, atol=1e-300)
+
+
 PINS = [pin_c2, pin_hitran_at_tref, pin_exomol_from_oscillator_strength, pin_hitran_exomol_consistency,
         pin_partition_table, pin_doppler_published, pin_lorentz_closed_forms, pin_voigt_gaussian_limit,
         pin_voigt_centre_erfcx, pin_voigt_lorentz_limit, pin_voigt_convolution_quadrature,
         pin_voigt_scipy_profile, pin_voigt_normalisation, pin_brute_equals_windowed, pin_single_line,
         pin_linearity_and_permutation, pin_grid_shift, pin_cutoff_inclusive, pin_count_evals_bruteforce,
         pin_points_equal_full, pin_nodes_uniform_equals_windowed, pin_nodes_bruteforce, pin_node_windows,
-        pin_fixed_resolution]
+        pin_fixed_resolution, pin_select_rules, pin_select_sum]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -391,3 +421,9 @@ def test_mutation_nodes_shifted(monkeypatch):
     real = orc.xsec_nodes
     monkeypatch.setattr(orc, "xsec_nodes", lambda L, nodes, *a, **k: real(L, np.asarray(nodes) + 1e-3, *a, **k))
     assert _fails(pin_nodes_uniform_equals_windowed) and _fails(pin_nodes_bruteforce)
+
+
+def test_mutation_select_threshold_inverted(monkeypatch):
+    real = orc.select_mask
+    monkeypatch.setattr(orc, "select_mask", lambda nu0, S, rel, b: ~real(nu0, S, rel, b) | (np.asarray(S) == 0))
+    assert _fails(pin_select_rules)
