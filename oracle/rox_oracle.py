@@ -33,10 +33,12 @@ Readings where the paper is silent (all listed in the design doc as well):
       lambda/dlambda), k = 0..K with K the largest index keeping nu_k <= nu_hi.
   R15 Main-contributor selection ("Compute line-strengths and -widths": the line-profile step
       can be sped up by keeping only the main line-strength contributors). At each (P,T), with
-      S = S(T) in float64: lines are binned by nu0 into bins of width B measured from the first
-      (smallest) nu0 of the sorted list, bin = floor((nu0 - nu0_first) / B); line i is kept iff
-      S_i >= rel * max(S over its bin). rel = 0 keeps every line; the strongest line of each
-      bin is always kept. The cross-section is then R8 over the kept lines.
+      S = S(T) in float64: lines are binned by nu0 into n_bins bins of width B starting at
+      origin = nu_min - cutoff, bin = floor((nu0 - origin) / B), n_bins =
+      floor(((n - 1) dnu + 2 cutoff) / B) + 1, which covers every nu0 that reaches a grid node;
+      line i is kept iff its bin is in range and S_i >= rel * max(S over its bin). rel = 0
+      keeps every line that can reach the grid; the strongest line of each bin is always kept.
+      The cross-section is then R8 over the kept lines.
 """
 import numpy as np
 from scipy.special import wofz
@@ -47,7 +49,7 @@ __all__ = [
     "voigt_profile", "grid_nodes", "window_indices", "count_evals",
     "xsec_bruteforce", "xsec_windowed", "xsec_points", "xsec_window", "sort_lines",
     "fixed_resolution_nodes", "node_windows", "xsec_nodes", "xsec_nodes_bruteforce",
-    "select_mask", "select_lines",
+    "select_bins", "select_mask", "select_lines",
 ]
 
 # R1: CODATA 2018 exact SI values where defined
@@ -319,23 +321,32 @@ def xsec_nodes(lines_sorted, nodes, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, ks=N
 
 
 # ---------------------------------------------------------------- R15: main-contributor selection
-def select_mask(nu0_sorted, S, rel, bin_width):
-    """R15: boolean mask of the kept lines (nu0 ascending, S float64 at one temperature)."""
-    nu0 = np.asarray(nu0_sorted, dtype=np.float64)
+def select_bins(grid, cutoff, bin_width):
+    """R15 bins of a uniform grid: (origin, n_bins)."""
+    nu_min, dnu, n = grid
+    origin = nu_min - cutoff
+    n_bins = int(np.floor(((n - 1) * dnu + 2.0 * cutoff) / bin_width)) + 1
+    return origin, n_bins
+
+
+def select_mask(nu0, S, rel, bin_width, origin, n_bins):
+    """R15: boolean mask of the kept lines (S float64 at one temperature)."""
+    nu0 = np.asarray(nu0, dtype=np.float64)
     S = np.asarray(S, dtype=np.float64)
-    if nu0.size == 0:
-        return np.zeros(0, dtype=bool)
-    b = np.floor((nu0 - nu0[0]) / float(bin_width)).astype(np.int64)
+    b = np.floor((nu0 - origin) / float(bin_width))
+    inr = (b >= 0) & (b < n_bins)
+    b = np.where(inr, b, 0).astype(np.int64)
     binmax = {}
-    for k, s in zip(b.tolist(), S.tolist()):
-        if k not in binmax or s > binmax[k]:
+    for k, s, ok in zip(b.tolist(), S.tolist(), inr.tolist()):
+        if ok and (k not in binmax or s > binmax[k]):
             binmax[k] = s
-    thr = np.array([float(rel) * binmax[k] for k in b.tolist()])
-    return S >= thr
+    thr = np.array([float(rel) * binmax[k] if ok else np.inf for k, ok in zip(b.tolist(), inr.tolist())])
+    return inr & (S >= thr)
 
 
-def select_lines(lines_sorted, T, Q_T, Q_ref, rel, bin_width):
-    """The kept lines of R15 at temperature T, as a line dict (same order)."""
+def select_lines(lines_sorted, grid, cutoff, T, Q_T, Q_ref, rel, bin_width):
+    """The kept lines of R15 at temperature T on a uniform grid, as a line dict (same order)."""
     S = line_strength(lines_sorted, T, Q_T, Q_ref)
-    keep = select_mask(lines_sorted["nu0"], S, rel, bin_width)
+    origin, n_bins = select_bins(grid, cutoff, bin_width)
+    keep = select_mask(lines_sorted["nu0"], S, rel, bin_width, origin, n_bins)
     return {k: (v[keep] if isinstance(v, np.ndarray) else v) for k, v in lines_sorted.items()}, keep

@@ -302,15 +302,19 @@ def pin_select_rules(o):
     rng = np.random.default_rng(13)
     nu0 = np.sort(rng.uniform(1000.0, 1100.0, 4000))
     S = 10.0 ** rng.uniform(-30, -18, nu0.size)
-    assert o.select_mask(nu0, S, 0.0, 1.0).all()                     # rel = 0 keeps every line
-    one = o.select_mask(nu0, S, 1.0, 1e9)                              # one bin, rel = 1: the strongest only
+    assert o.select_mask(nu0, S, 0.0, 1.0, 990.0, 200).all()           # rel = 0 keeps every line in range
+    one = o.select_mask(nu0, S, 1.0, 1e9, 0.0, 1)                      # one bin, rel = 1: the strongest only
     assert one.sum() == 1 and S[one][0] == S.max()
-    m = o.select_mask(nu0, S, 1e-3, 1.0)
-    b = np.floor((nu0 - nu0[0]) / 1.0).astype(int)
+    m = o.select_mask(nu0, S, 1e-3, 1.0, 990.5, 200)
+    b = np.floor(nu0 - 990.5).astype(int)
     for k in np.unique(b):                                             # brute force per bin
         sel = b == k
         assert np.array_equal(m[sel], S[sel] >= 1e-3 * S[sel].max())
-    assert o.select_mask(nu0, S, 1e-2, 1.0).sum() <= m.sum() <= o.select_mask(nu0, S, 1e-4, 1.0).sum()
+    assert (o.select_mask(nu0, S, 1e-2, 1.0, 990.5, 200).sum() <= m.sum()
+            <= o.select_mask(nu0, S, 1e-4, 1.0, 990.5, 200).sum())
+    part = o.select_mask(nu0, S, 0.0, 1.0, 1050.0, 20)                 # bins cover [1050, 1070) only
+    assert np.array_equal(part, (nu0 >= 1050.0) & (nu0 < 1070.0))
+    assert o.select_bins((2000.0, 0.01, 50001), 25.0, 1.0) == (1975.0, 551)
 
 
 def pin_select_sum(o):
@@ -318,9 +322,9 @@ def pin_select_sum(o):
     L = _small(n=60)
     P, T, Qt, Qr, mass, cut = ARGS
     full = o.xsec_windowed(L, GRID, *ARGS)
-    L0, keep0 = o.select_lines(L, T, Qt, Qr, 0.0, 1.0)
-    assert keep0.all() and np.array_equal(o.xsec_windowed(L0, GRID, *ARGS), full)
-    Lk, keep = o.select_lines(L, T, Qt, Qr, 1e-3, 5.0)
+    L0, keep0 = o.select_lines(L, GRID, cut, T, Qt, Qr, 0.0, 1.0)
+    assert np.array_equal(o.xsec_windowed(L0, GRID, *ARGS), full)
+    Lk, keep = o.select_lines(L, GRID, cut, T, Qt, Qr, 1e-3, 5.0)
     assert 0 < keep.sum() < keep.size
     drop = {k: (v[~keep] if isinstance(v, np.ndarray) else v) for k, v in L.items()}
     assert np.allclose(o.xsec_windowed(Lk, GRID, *ARGS) + o.xsec_windowed(drop, GRID, *ARGS), full,
@@ -425,5 +429,5 @@ def test_mutation_nodes_shifted(monkeypatch):
 
 def test_mutation_select_threshold_inverted(monkeypatch):
     real = orc.select_mask
-    monkeypatch.setattr(orc, "select_mask", lambda nu0, S, rel, b: ~real(nu0, S, rel, b) | (np.asarray(S) == 0))
+    monkeypatch.setattr(orc, "select_mask", lambda nu0, S, rel, b, og, nb: ~real(nu0, S, rel, b, og, nb))
     assert _fails(pin_select_rules)
