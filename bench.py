@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--lines", type=int, default=None,
                     help="use only the first N lines of the workload (smaller profiling case)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (request-latency) leg")
+    ap.add_argument("--select", type=float, default=None, metavar="REL",
+                    help="main-contributor selection: keep lines with S >= REL x the largest S of their nu0 bin "
+                         "(rox_xsec_select_batch)")
+    ap.add_argument("--select-bin", type=float, default=1.0, help="selection bin width (cm^-1)")
     ap.add_argument("--nodes", action="store_true",
                     help="user-provided grid: the workload's lines on nodes of fixed resolving power R = %g over the "
                          "same wavenumber range (rox_xsec_nodes_batch)" % rs.FIXED_R)
@@ -302,6 +306,8 @@ def run_gpu(args):
     n = len(host["nu0"])
     h2d_bytes = sum(v.numel() * v.element_size() for v in pinned.values())
     sort_ws = torch.empty(rox.rox_sort_workspace_size(n), dtype=torch.uint8, device=dev)
+    if args.nodes and args.select is not None:
+        raise SystemExit("--select runs on the uniform grid only")
     if args.nodes:
         nodes_np = rs.fixed_resolution_grid(w.grid_lo, w.grid_hi, rs.FIXED_R)
         nodes_pin = torch.from_numpy(nodes_np).pin_memory()
@@ -310,6 +316,10 @@ def run_gpu(args):
         n_grid = nodes_np.size
         h2d_bytes += n_grid * 8
         ws = torch.empty(rox.rox_xsec_nodes_workspace_size(n, n_grid, 1), dtype=torch.uint8, device=dev)
+    elif args.select is not None:
+        n_grid = grid[2]
+        ws = torch.empty(rox.rox_xsec_select_workspace_size(n, grid, 1, w.cutoff, args.select, args.select_bin),
+                         dtype=torch.uint8, device=dev)
     else:
         n_grid = grid[2]
         ws = torch.empty(rox.rox_xsec_workspace_size(n, grid, 1), dtype=torch.uint8, device=dev)
@@ -327,6 +337,9 @@ def run_gpu(args):
     def step():
         if args.nodes:
             rox.rox_xsec_nodes_batch(lines, nodes_dev, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws)
+        elif args.select is not None:
+            rox.rox_xsec_select_batch(lines, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, args.select,
+                                      args.select_bin, sigma, ws)
         else:
             rox.rox_xsec(lines, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
 
@@ -434,7 +447,12 @@ def run_gpu(args):
                                        w.name, n, "ExoMol" if w.convention == 1 else "HITRAN", rs.FIXED_R, w.grid_lo,
                                        w.grid_hi, n_grid, w.cutoff, P, T)),
                            "evals_per_step": evals, "xsecs_per_s": world * args.steps / (ms * 1e-3),
-                           "step": ("rox_xsec_nodes_batch" if args.nodes else "rox_xsec") +
+                           "selection": None if args.select is None else {
+                               "rel": args.select, "bin_width_cm": args.select_bin,
+                               "note": "value counts the kept (line, point) pairs; xsecs_per_s is the like-for-like "
+                                       "speed against the unselected run"},
+                           "step": ("rox_xsec_nodes_batch" if args.nodes else
+                                    "rox_xsec_select_batch" if args.select is not None else "rox_xsec") +
                                    " on the resident nu0-sorted list (strengths, widths, windows, tile "
                                    "ranges, Voigt accumulate); the once-per-list sort is inside e2e",
                            "l2": "inputs larger than L2 (line list %.0f MB, workspace %.0f MB)" % (
@@ -446,7 +464,7 @@ def run_gpu(args):
                         "ms_per_step": e2e_ms / e2e_steps if e2e_steps else None,
                         "includes": "H2D of the unsorted list%s, rox_sort_lines, %s, D2H of sigma" % (
                             " and the nodes" if args.nodes else "", "rox_xsec_nodes_batch" if args.nodes else "rox_xsec")},
-                "gpu_launches": args.steps * (6 if args.nodes else 5),
+                "gpu_launches": args.steps * (6 if args.nodes else 7 if args.select is not None else 5),
                 "gpu_launches_note": "per step: %swindows, strengths, strength scaling, tile ranges, Voigt kernels "
                                      "(+ memsets)" % ("node offsets, " if args.nodes else ""),
                 "clocks": csum}

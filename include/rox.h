@@ -66,6 +66,7 @@ extern "C" {
 #define ROX_MAX_PT 512            /* (P,T) points per rox_xsec_batch call */
 #define ROX_MAX_GRID (1 << 23)    /* grid points (line-centre indices are carried exactly in FP32) */
 #define ROX_MAX_CUTOFF_STEPS (1 << 21) /* cutoff / dnu */
+#define ROX_MAX_SELECT_BINS (1 << 24)  /* bins of a main-contributor selection */
 
 /* A line list as structure-of-arrays, n lines, all DEVICE pointers.
  * nu0       [n] double  line centre (cm^-1), > 0
@@ -188,6 +189,39 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt,
 int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double T,
              double Q_T, double Q_ref, double mass_amu, double cutoff, float* sigma_out,
              void* ws, size_t ws_bytes, void* stream);
+
+/* a4/a5 with main-contributor line selection (paper, "Compute line-strengths and -widths": the
+ * line-profile step can be sped up by keeping only the main line-strength contributors).
+ * At each (P,T) point, with S = S(T) in double precision, the lines are binned by nu0 into
+ * bins of width bin_width (cm^-1) starting at grid->nu_min - cutoff,
+ *   bin = floor((nu0 - (nu_min - cutoff)) / bin_width)   (subtraction and division each rounded
+ *                                                         once in double precision),
+ * n_bins = floor(((grid->n - 1) dnu + 2 cutoff) / bin_width) + 1 (every nu0 that reaches a grid
+ * point falls in a bin), and a line is kept iff its bin is in range and
+ * S >= rel * (the largest S in its bin at that temperature) (product rounded once). rel = 0
+ * keeps every line that reaches the grid; each bin keeps at least its strongest line.
+ * sigma_out is the cross-section of the kept lines (R8 over them); dropped lines cost no
+ * profile evaluation, and rox_ws_status counts the kept (line, grid point) pairs only.
+ * Arguments otherwise as rox_xsec_batch; sel->rel >= 0, sel->bin_width > 0, n_bins <=
+ * ROX_MAX_SELECT_BINS. ws: rox_xsec_select_workspace_size(lines->n, grid, n_temps, cutoff, sel)
+ * bytes (0 if the selection is invalid). */
+typedef struct rox_select {
+  double rel;
+  double bin_width;
+} rox_select;
+size_t rox_xsec_select_workspace_size(int64_t n_lines, const rox_grid* grid, int n_temps, double cutoff,
+                                      const rox_select* sel);
+int rox_xsec_select_batch(const rox_lines* lines, const rox_grid* grid, int n_pt,
+                          const double* P_bar, const double* T, const double* Q_T, double Q_ref,
+                          double mass_amu, double cutoff, unsigned flags, const rox_select* sel,
+                          float* sigma_out, void* ws, size_t ws_bytes, void* stream);
+
+/* The selection of rox_xsec_select_batch at one temperature: keep_out[i] = 1 if line i is
+ * kept, else 0 ([lines->n] uint8, device). Widths are not needed (gamma_ref and n_t may be
+ * NULL). ws: rox_xsec_select_workspace_size(lines->n, grid, 1, cutoff, sel) bytes. */
+int rox_line_select(const rox_lines* lines, const rox_grid* grid, double cutoff, double T,
+                    double Q_T, double Q_ref, const rox_select* sel, uint8_t* keep_out,
+                    void* ws, size_t ws_bytes, void* stream);
 
 /* a4/a5 on user-provided nodes (paper, "Similar tools": any user-provided wavelength or
  * wavenumber grid, which fixes the resolving power R = lambda/dlambda): rox_xsec_batch with the

@@ -46,6 +46,10 @@ class RoxNodes(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_void_p), ("n", ctypes.c_int64)]
 
 
+class RoxSelect(ctypes.Structure):
+    _fields_ = [("rel", ctypes.c_double), ("bin_width", ctypes.c_double)]
+
+
 class RoxPrepared(ctypes.Structure):
     _fields_ = [("lines", RoxLines), ("lattice", RoxGrid), ("cutoff", ctypes.c_double), ("state", ctypes.c_void_p),
                 ("span_lo", ctypes.c_void_p), ("span_hi", ctypes.c_void_p), ("n_spans", ctypes.c_int64)]
@@ -87,6 +91,10 @@ def _load():
         "rox_xsec_nodes_workspace_size": (ctypes.c_size_t, [I64, I64, ctypes.c_int]),
         "rox_xsec_nodes_batch": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P, ctypes.c_size_t, P]),
         "rox_node_windows": (ctypes.c_int, [P, I64, P, D, P, P, P]),
+        "rox_xsec_select_workspace_size": (ctypes.c_size_t, [I64, P, ctypes.c_int, D, P]),
+        "rox_xsec_select_batch": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P, P, ctypes.c_size_t,
+                                                 P]),
+        "rox_line_select": (ctypes.c_int, [P, P, D, D, D, D, P, P, P, ctypes.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -220,6 +228,33 @@ def rox_node_windows(nu0, nodes, cutoff, jlo, jhi, stream=None):
     N = nodes_struct(nodes)
     _check(lib.rox_node_windows(_ptr(nu0), nu0.numel(), ctypes.byref(N), cutoff, _ptr(jlo), _ptr(jhi),
                                 _stream(stream)))
+
+
+def rox_xsec_select_workspace_size(n_lines, grid, n_temps, cutoff, rel, bin_width):
+    G = grid_struct(grid)
+    S = RoxSelect(float(rel), float(bin_width))
+    return lib.rox_xsec_select_workspace_size(n_lines, ctypes.byref(G), n_temps, cutoff, ctypes.byref(S))
+
+
+def rox_xsec_select_batch(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, rel, bin_width, sigma_out, ws, flags=0,
+                          stream=None):
+    """rox_xsec_batch keeping only the main line-strength contributors (rel, bin_width)."""
+    n_pt = len(P_bar)
+    arr = ctypes.c_double * n_pt
+    L = lines_struct(lines)
+    G = grid_struct(grid)
+    S = RoxSelect(float(rel), float(bin_width))
+    _check(lib.rox_xsec_select_batch(ctypes.byref(L), ctypes.byref(G), n_pt, arr(*P_bar), arr(*T), arr(*Q_T), Q_ref,
+                                     mass_amu, cutoff, flags, ctypes.byref(S), _ptr(sigma_out), _ptr(ws), ws.numel(),
+                                     _stream(stream)))
+
+
+def rox_line_select(lines, grid, cutoff, T, Q_T, Q_ref, rel, bin_width, keep_out, ws, stream=None):
+    L = lines_struct(lines)
+    G = grid_struct(grid)
+    S = RoxSelect(float(rel), float(bin_width))
+    _check(lib.rox_line_select(ctypes.byref(L), ctypes.byref(G), cutoff, T, Q_T, Q_ref, ctypes.byref(S),
+                               _ptr(keep_out), _ptr(ws), ws.numel(), _stream(stream)))
 
 
 def rox_xsec(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, stream=None):

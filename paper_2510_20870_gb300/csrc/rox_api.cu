@@ -40,6 +40,11 @@ cudaError_t rox_launch_node_offsets(const double* nodes, long long n, long long 
 void rox_fill_strength_consts(int convention, double T, double Q_T, double Q_ref, RoxStrengthJob* jb);
 cudaError_t rox_launch_strengths_jobs(const RoxStrengthJobs& J, long long max_count, cudaStream_t s);
 cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes);
+cudaError_t rox_launch_select(const double* nu0, const double* S_T, long long n, int n_temps,
+                              const unsigned long long* smax_bits, double origin, double width, long long n_bins,
+                              double rel, int32_t* bin, unsigned long long* binmax_bits, float* S32, cudaStream_t s);
+cudaError_t rox_launch_keep_flags(const double* S_T, const int32_t* bin, const unsigned long long* binmax_bits,
+                                  long long n, double rel, uint8_t* keep, cudaStream_t s);
 cudaError_t rox_launch_faddeeva(const float* x, const float* y, float* out, long long n, cudaStream_t s);
 
 namespace {
@@ -124,10 +129,13 @@ struct WsLayout {
   long long tail_cap;
   float2* node_d;      // user-provided nodes only: [n_tiles * ROX_SPAN] offsets, [n_tiles] bases
   float2* span_base;
+  int32_t* line_bin;   // main-contributor selection only: [n_lines] bins, [n_temps][n_bins] maxima
+  unsigned long long* binmax;
   size_t bytes;
 };
 
-WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, bool nodes = false) {
+WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, bool nodes = false,
+                   long long n_bins = 0) {
   WsLayout w;
   char* base = (char*)ws;
   size_t off = 0;
@@ -156,8 +164,29 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, b
     w.span_base = (float2*)(base + off);
     off += rox_align256((size_t)nt * sizeof(float2));
   }
+  w.line_bin = nullptr;
+  w.binmax = nullptr;
+  if (n_bins > 0) {
+    w.line_bin = (int32_t*)(base + off);
+    off += rox_align256((size_t)(n_lines > 0 ? n_lines : 1) * 4);
+    w.binmax = (unsigned long long*)(base + off);
+    off += rox_align256((size_t)n_temps * (size_t)n_bins * 8);
+  }
   w.bytes = off;
   return w;
+}
+
+// main-contributor selection bins of a uniform grid: origin nu_min - cutoff, width B
+int select_bins(const rox_select* sel, const rox_grid* g, double cutoff, double* origin, long long* n_bins) {
+  if (!sel) return fail(ROX_EINVAL, "selection is NULL");
+  if (!std::isfinite(sel->rel) || sel->rel < 0.0) return fail(ROX_EINVAL, "selection rel must be >= 0");
+  if (!finite_pos(sel->bin_width)) return fail(ROX_EINVAL, "selection bin_width must be > 0");
+  const double nb = std::floor(((double)(g->n - 1) * g->dnu + 2.0 * cutoff) / sel->bin_width) + 1.0;
+  if (!(nb <= (double)ROX_MAX_SELECT_BINS))
+    return fail(ROX_ERANGE, "%g selection bins above %d (bin_width too small)", nb, ROX_MAX_SELECT_BINS);
+  *origin = g->nu_min - cutoff;
+  *n_bins = (long long)nb;
+  return ROX_OK;
 }
 
 int g_voigt_blocks[2] = {0, 0};
@@ -313,10 +342,14 @@ namespace {
 // other NULL; both checked by the caller.
 int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_nodes* nodes, int n_pt,
                     const double* P_bar, const double* T, const double* Q_T, double Q_ref, double mass_amu,
-                    double cutoff, unsigned flags, float* sigma_out, void* ws, size_t ws_bytes, void* stream) {
+                    double cutoff, unsigned flags, float* sigma_out, void* ws, size_t ws_bytes, void* stream,
+                    const rox_select* sel = nullptr) {
   int rc = check_lines(lines, true, true);
   if (rc) return rc;
   const bool on_nodes = nodes != nullptr;
+  double sel_origin = 0.0;
+  long long n_bins = 0;
+  if (sel && (rc = select_bins(sel, grid, cutoff, &sel_origin, &n_bins))) return rc;
   const long long n_grid = on_nodes ? nodes->n : grid->n;
   if (n_pt < 1 || n_pt > ROX_MAX_PT) return fail(ROX_EINVAL, "n_pt = %d outside [1, %d]", n_pt, ROX_MAX_PT);
   if (!P_bar || !T || !Q_T) return fail(ROX_EINVAL, "P_bar, T, Q_T host arrays required");
@@ -343,7 +376,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   }
   const int n_temps = (int)temps.size();
   if (!ws || ((uintptr_t)ws & 255)) return fail(ROX_EINVAL, "workspace NULL or not 256-byte aligned");
-  WsLayout w = ws_layout(ws, lines->n, n_grid, n_temps, on_nodes);
+  WsLayout w = ws_layout(ws, lines->n, n_grid, n_temps, on_nodes, n_bins);
   if (ws_bytes < w.bytes) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.bytes);
 
   cudaStream_t s = (cudaStream_t)stream;
@@ -369,9 +402,11 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
                                                     w.hdr->smax_bits, s),
                          "strengths kernel")))
       return rc;
-    if ((rc = cuda_check(rox_launch_scale_strengths(w.S_T, nl, n_temps, w.hdr->smax_bits, w.S32, s),
-                         "strength scaling kernel")))
-      return rc;
+    const cudaError_t se =
+        sel ? rox_launch_select(lines->nu0, w.S_T, nl, n_temps, w.hdr->smax_bits, sel_origin, sel->bin_width, n_bins,
+                                sel->rel, w.line_bin, w.binmax, w.S32, s)
+            : rox_launch_scale_strengths(w.S_T, nl, n_temps, w.hdr->smax_bits, w.S32, s);
+    if ((rc = cuda_check(se, "strength scaling kernel"))) return rc;
   }
   if ((rc = cuda_check(rox_launch_tile_ranges_geo(w.geo, nl, nt, ROX_TILE, w.tlo, w.thi, s), "tile ranges")))
     return rc;
@@ -425,6 +460,60 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
   if ((rc = check_cutoff(cutoff, grid))) return rc;
   return xsec_batch_impl(lines, grid, nullptr, n_pt, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, flags, sigma_out, ws,
                          ws_bytes, stream);
+}
+
+size_t rox_xsec_select_workspace_size(int64_t n_lines, const rox_grid* grid, int n_temps, double cutoff,
+                                      const rox_select* sel) {
+  if (!grid || grid->n <= 0 || n_lines < 0 || n_temps <= 0 || !sel || !finite_pos(sel->bin_width) ||
+      !finite_pos(cutoff))
+    return 0;
+  double origin;
+  long long n_bins;
+  if (select_bins(sel, grid, cutoff, &origin, &n_bins)) return 0;
+  return ws_layout(nullptr, n_lines, grid->n, n_temps, false, n_bins).bytes;
+}
+
+int rox_xsec_select_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const double* P_bar,
+                          const double* T, const double* Q_T, double Q_ref, double mass_amu, double cutoff,
+                          unsigned flags, const rox_select* sel, float* sigma_out, void* ws, size_t ws_bytes,
+                          void* stream) {
+  int rc;
+  if ((rc = check_grid(grid))) return rc;
+  if ((rc = check_cutoff(cutoff, grid))) return rc;
+  if (!sel) return fail(ROX_EINVAL, "selection is NULL");
+  return xsec_batch_impl(lines, grid, nullptr, n_pt, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, flags, sigma_out, ws,
+                         ws_bytes, stream, sel);
+}
+
+int rox_line_select(const rox_lines* lines, const rox_grid* grid, double cutoff, double T, double Q_T, double Q_ref,
+                    const rox_select* sel, uint8_t* keep_out, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_lines(lines, true, false);
+  if (rc) return rc;
+  if ((rc = check_grid(grid))) return rc;
+  if ((rc = check_cutoff(cutoff, grid))) return rc;
+  if (!finite_pos(T) || !finite_pos(Q_T) || !finite_pos(Q_ref)) return fail(ROX_EINVAL, "T, Q_T, Q_ref must be > 0");
+  if (!keep_out) return fail(ROX_EINVAL, "keep_out is NULL");
+  double origin;
+  long long n_bins;
+  if ((rc = select_bins(sel, grid, cutoff, &origin, &n_bins))) return rc;
+  if (!ws || ((uintptr_t)ws & 255)) return fail(ROX_EINVAL, "workspace NULL or not 256-byte aligned");
+  WsLayout w = ws_layout(ws, lines->n, grid->n, 1, false, n_bins);
+  if (ws_bytes < w.bytes) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.bytes);
+  const long long nl = lines->n;
+  if (nl == 0) return ok();
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = cuda_check(cudaMemsetAsync(w.hdr, 0, sizeof(RoxWsHeader), s), "memset"))) return rc;
+  if ((rc = cuda_check(rox_launch_strengths_multi(lines, 1, &T, &Q_T, Q_ref, w.S_T, w.hdr->smax_bits, s),
+                       "strengths kernel")))
+    return rc;
+  if ((rc = cuda_check(rox_launch_select(lines->nu0, w.S_T, nl, 1, w.hdr->smax_bits, origin, sel->bin_width, n_bins,
+                                         sel->rel, w.line_bin, w.binmax, w.S32, s),
+                       "selection kernels")))
+    return rc;
+  if ((rc = cuda_check(rox_launch_keep_flags(w.S_T, w.line_bin, w.binmax, nl, sel->rel, keep_out, s),
+                       "keep flags kernel")))
+    return rc;
+  return ok();
 }
 
 size_t rox_xsec_nodes_workspace_size(int64_t n_lines, int64_t n_nodes, int n_temps) {

@@ -82,14 +82,80 @@ __global__ void k_strengths_multi(rox_lines L, TempSet ts,
 
 // S * 2^-e per temperature, e the exponent of the largest strength at that temperature,
 // so the Voigt kernel works in FP32 well inside its range whatever the line strengths are.
+// S * 2^-e in FP32 (e the exponent of the temperature's largest S). With a selection
+// (bin != NULL): lines outside the bins, or below rel times their bin's largest S at that
+// temperature (the product rounded once in double precision), get -0.0, which the Voigt kernel
+// tells apart from a kept strength that rounds to +0.0 in FP32.
 __global__ void k_scale_strengths(const double* __restrict__ S_T, long long n, int n_temps,
-                                  const unsigned long long* __restrict__ smax_bits, float* S32) {
+                                  const unsigned long long* __restrict__ smax_bits, float* S32,
+                                  const int32_t* __restrict__ bin, const unsigned long long* __restrict__ binmax_bits,
+                                  long long n_bins, double rel) {
   long long stride = (long long)gridDim.x * blockDim.x;
   for (int t = 0; t < n_temps; t++) {
     double smax = __longlong_as_double((long long)smax_bits[t]);
     double sc = ldexp(1.0, smax > 0.0 ? -ilogb(smax) : 0);
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-      S32[(long long)t * n + i] = (float)(S_T[(long long)t * n + i] * sc);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const double S = S_T[(long long)t * n + i];
+      bool keep = true;
+      if (bin) {
+        const int b = bin[i];
+        keep = b >= 0 &&
+               S >= __dmul_rn(rel, __longlong_as_double((long long)binmax_bits[(long long)t * n_bins + b]));
+      }
+      S32[(long long)t * n + i] = keep ? (float)(S * sc) : -0.0f;   // -0: dropped (+0: kept, below FP32)
+    }
+  }
+}
+
+// Main-contributor selection, bin of every line: floor((nu0 - origin) / width) with the
+// subtraction and the division each rounded once in double precision; -1 outside [0, n_bins).
+__global__ void k_line_bins(const double* __restrict__ nu0, long long n, double origin, double width,
+                            long long n_bins, int32_t* bin) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double b = floor(__ddiv_rn(__dsub_rn(nu0[i], origin), width));
+    bin[i] = (b >= 0.0 && b < (double)n_bins) ? (int32_t)b : -1;
+  }
+}
+
+// Largest S per temperature and bin (as double bits; S >= 0, so the bit patterns order like
+// the values). The list is sorted by nu0, so each bin is a run of lines: every thread folds
+// a run of ROX_BIN_RUN consecutive lines and issues one atomic max per bin it meets.
+#define ROX_BIN_RUN 16
+__global__ void k_bin_max(const int32_t* __restrict__ bin, const double* __restrict__ S_T, long long n, int n_temps,
+                          long long n_bins, unsigned long long* binmax_bits) {
+  const long long runs = (n + ROX_BIN_RUN - 1) / ROX_BIN_RUN;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (int t = 0; t < n_temps; t++) {
+    const double* S = S_T + (long long)t * n;
+    unsigned long long* bm = binmax_bits + (long long)t * n_bins;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < runs; r += stride) {
+      const long long i0 = r * ROX_BIN_RUN, i1 = min(n, i0 + ROX_BIN_RUN);
+      int cur = -1;
+      double mx = 0.0;
+      for (long long i = i0; i < i1; i++) {
+        const int b = bin[i];
+        if (b != cur) {
+          if (cur >= 0) atomicMax(&bm[cur], (unsigned long long)__double_as_longlong(mx));
+          cur = b;
+          mx = S[i];
+        } else {
+          mx = fmax(mx, S[i]);
+        }
+      }
+      if (cur >= 0) atomicMax(&bm[cur], (unsigned long long)__double_as_longlong(mx));
+    }
+  }
+}
+
+// keep flags of the first temperature: the same test as k_scale_strengths
+__global__ void k_keep_flags(const double* __restrict__ S_T, const int32_t* __restrict__ bin,
+                             const unsigned long long* __restrict__ binmax_bits, long long n, double rel,
+                             uint8_t* keep) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int b = bin[i];
+    keep[i] = b >= 0 && S_T[i] >= __dmul_rn(rel, __longlong_as_double((long long)binmax_bits[b]));
   }
 }
 
@@ -193,6 +259,23 @@ cudaError_t rox_launch_strengths_jobs(const RoxStrengthJobs& J, long long max_co
 
 cudaError_t rox_launch_scale_strengths(const double* S_T, long long n, int n_temps,
                                        const unsigned long long* smax_bits, float* S32, cudaStream_t s) {
-  k_scale_strengths<<<grid_for(n), 256, 0, s>>>(S_T, n, n_temps, smax_bits, S32);
+  k_scale_strengths<<<grid_for(n), 256, 0, s>>>(S_T, n, n_temps, smax_bits, S32, nullptr, nullptr, 0, 0.0);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_select(const double* nu0, const double* S_T, long long n, int n_temps,
+                              const unsigned long long* smax_bits, double origin, double width, long long n_bins,
+                              double rel, int32_t* bin, unsigned long long* binmax_bits, float* S32, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(binmax_bits, 0, (size_t)n_temps * (size_t)n_bins * 8, s);
+  if (e != cudaSuccess) return e;
+  k_line_bins<<<grid_for(n), 256, 0, s>>>(nu0, n, origin, width, n_bins, bin);
+  k_bin_max<<<grid_for((n + ROX_BIN_RUN - 1) / ROX_BIN_RUN), 256, 0, s>>>(bin, S_T, n, n_temps, n_bins, binmax_bits);
+  k_scale_strengths<<<grid_for(n), 256, 0, s>>>(S_T, n, n_temps, smax_bits, S32, bin, binmax_bits, n_bins, rel);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_keep_flags(const double* S_T, const int32_t* bin, const unsigned long long* binmax_bits,
+                                  long long n, double rel, uint8_t* keep, cudaStream_t s) {
+  k_keep_flags<<<grid_for(n), 256, 0, s>>>(S_T, bin, binmax_bits, n, rel, keep);
   return cudaGetLastError();
 }

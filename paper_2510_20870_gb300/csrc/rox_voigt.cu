@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
 
         // ---- per-line constants (lane <-> line b0 + lane)
         Rec r;
+        bool has_S = false;   // zero strength (below FP32, or -0.0: dropped by a selection): nothing to add
         if (lane < cnt) {
           const float4 g = geo_st[buf][lane];
           const float Sp = S_st[buf][lane];
@@ -337,8 +338,10 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
           }
           const float gG = nu0f * J.gG_fac;
           const float gL = gref * exp2f(nt * J.l2_ratio) * J.p_fac;
+          has_S = Sp != 0.0f;
+          const bool dropped = __float_as_uint(Sp) == 0x80000000u;   // -0.0: not kept by a selection
           const long long ov = min((long long)jhi, whi) - max((long long)jlo, wlo) + 1;
-          if (ov > 0) evals += (unsigned long long)ov;
+          if (ov > 0 && !dropped) evals += (unsigned long long)ov;
           const float gG2 = gG * gG, gL2 = gL * gL;
           const float pY = Sp * gL * ROX_INV_PI;
           const float invG = 1.0f / gG;
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         // unmasked pairs; covering lines with a slow zone in masked pairs; window-edge lines in
         // pairs with window masks. The orders are fixed, so the sum is reproducible.
         const unsigned cls = __float_as_uint(r.b.z);
-        const bool live = lane < cnt;
+        const bool live = lane < cnt && has_S;
         unsigned cmask = __ballot_sync(0xffffffffu, live && cls == 1u);
         unsigned zmask = __ballot_sync(0xffffffffu, live && cls == 3u);
         const unsigned emask = __ballot_sync(0xffffffffu, live && !(cls & 1u));
