@@ -39,6 +39,14 @@ Readings where the paper is silent (all listed in the design doc as well):
       line i is kept iff its bin is in range and S_i >= rel * max(S over its bin). rel = 0
       keeps every line that can reach the grid; the strongest line of each bin is always kept.
       The cross-section is then R8 over the kept lines.
+  R16 Pressure-broadening descriptions ("Compute line-strengths and -widths": various
+      descriptions are supported; none is printed) and natural broadening:
+        gamma_L = sum_b x_b gamma_ref_b (T_ref/T)^n_b (P / P_ref)  +  [A / (4 pi c)]
+      over broadeners b with mixing ratios x_b (up to 4), each broadener's (gamma_ref_b, n_b)
+      per line, either given as columns or looked up in a table by the line's lower-state J
+      (J beyond the table takes its last entry); the natural term (Lorentz HWHM of the
+      Einstein-A decay, c in cm/s) only for ExoMol lists, where s_or_a is A. Lorentz widths
+      add, as Lorentzians convolve into one.
 """
 import numpy as np
 from scipy.special import wofz
@@ -49,7 +57,7 @@ __all__ = [
     "voigt_profile", "grid_nodes", "window_indices", "count_evals",
     "xsec_bruteforce", "xsec_windowed", "xsec_points", "xsec_window", "sort_lines",
     "fixed_resolution_nodes", "node_windows", "xsec_nodes", "xsec_nodes_bruteforce",
-    "select_bins", "select_mask", "select_lines",
+    "select_bins", "select_mask", "select_lines", "apply_broadening", "lorentz_width_broadened",
 ]
 
 # R1: CODATA 2018 exact SI values where defined
@@ -168,8 +176,45 @@ def sort_lines(lines):
 def _line_params(lines, P_bar, T, Q_T, Q_ref, mass_amu):
     S = line_strength(lines, T, Q_T, Q_ref)
     gG = doppler_width(lines["nu0"], T, mass_amu)
-    gL = lorentz_width(lines["gamma_ref"], lines["n_t"], P_bar, T)
+    if "vmr" in lines:
+        gL = lorentz_width_broadened(lines, P_bar, T)
+    else:
+        gL = lorentz_width(lines["gamma_ref"], lines["n_t"], P_bar, T)
     return S, gG, gL
+
+
+def apply_broadening(lines, vmr, gamma_ref=None, n_t=None, j_lower=None, table_gamma=None, table_n=None,
+                     natural=False):
+    """R16: the line dict with per-line columns gamma_b<k>, n_b<k> of each broadener k (from the
+    columns gamma_ref[k], n_t[k], or looked up in table_gamma[k], table_n[k] by j_lower, the
+    last entry for J beyond the table), the mixing ratios and the natural-broadening switch."""
+    out = dict(lines)
+    nb = len(vmr)
+    for k in range(nb):
+        if table_gamma is not None and table_gamma[k] is not None:
+            tg = np.asarray(table_gamma[k], dtype=np.float64)
+            tn = np.asarray(table_n[k], dtype=np.float64)
+            j = np.minimum(np.asarray(j_lower, dtype=np.int64), tg.size - 1)
+            out["gamma_b%d" % k] = tg[j]
+            out["n_b%d" % k] = tn[j]
+        else:
+            out["gamma_b%d" % k] = np.asarray(gamma_ref[k], dtype=np.float64)
+            out["n_b%d" % k] = np.asarray(n_t[k], dtype=np.float64)
+    out["vmr"] = tuple(float(x) for x in vmr)
+    out["natural"] = bool(natural)
+    return out
+
+
+def lorentz_width_broadened(lines, P_bar, T):
+    """R16. Lorentz HWHM (cm^-1) of a line dict prepared by apply_broadening."""
+    g = np.zeros(np.asarray(lines["nu0"]).size, dtype=np.float64)
+    for k, x in enumerate(lines["vmr"]):
+        g = g + x * lorentz_width(lines["gamma_b%d" % k], lines["n_b%d" % k], P_bar, T)
+    if lines["natural"]:
+        if lines["convention"] != EXOMOL:
+            raise ValueError("natural broadening needs Einstein A (ExoMol lists)")
+        g = g + np.asarray(lines["s_or_a"], dtype=np.float64) / (4.0 * np.pi * C_LIGHT_CM)
+    return g
 
 
 def xsec_bruteforce(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff):

@@ -331,13 +331,54 @@ def pin_select_sum(o):
                        rtol=1e-13, atol=1e-300)
 
 
+# ---------------------------------------------------------------- broadening descriptions (R16)
+def pin_broadening_single_equals_power_law(o):
+    L = _small(n=50)
+    B = o.apply_broadening(L, [1.0], gamma_ref=[L["gamma_ref"]], n_t=[L["n_t"]])
+    for P, T in ((1.0, 1000.0), (1e-3, 300.0), (50.0, 3000.0)):
+        assert np.array_equal(o.lorentz_width_broadened(B, P, T), o.lorentz_width(L["gamma_ref"], L["n_t"], P, T))
+    assert np.array_equal(o.xsec_windowed(B, GRID, *ARGS), o.xsec_windowed(L, GRID, *ARGS))
+
+
+def pin_broadening_mixture(o):
+    L = _small(n=40)
+    g1, n1 = np.full(40, 0.08), np.full(40, 0.5)      # e.g. H2
+    g2, n2 = np.full(40, 0.03), np.full(40, 0.7)      # e.g. He
+    B = o.apply_broadening(L, [0.85, 0.15], gamma_ref=[g1, g2], n_t=[n1, n2])
+    P, T = 3.0, 800.0
+    expect = (0.85 * 0.08 * (296.0 / 800.0) ** 0.5 + 0.15 * 0.03 * (296.0 / 800.0) ** 0.7) * 3.0 / 1.01325
+    assert np.allclose(o.lorentz_width_broadened(B, P, T), expect, rtol=1e-14, atol=0)
+    same = o.apply_broadening(L, [0.3, 0.7], gamma_ref=[g1, g1], n_t=[n1, n1])   # split of one broadener
+    one = o.apply_broadening(L, [1.0], gamma_ref=[g1], n_t=[n1])
+    assert np.allclose(o.lorentz_width_broadened(same, P, T), o.lorentz_width_broadened(one, P, T), rtol=1e-15)
+
+
+def pin_broadening_table_and_natural(o):
+    L = _small(n=30, conv=1)
+    J = np.arange(30) * 3                              # 0..87, beyond the 50-entry table from J = 50
+    tg = 0.1 - 0.001 * np.arange(50)
+    tn = 0.75 - 0.002 * np.arange(50)
+    B = o.apply_broadening(L, [1.0], j_lower=J, table_gamma=[tg], table_n=[tn])
+    jj = np.minimum(J, 49)
+    assert np.array_equal(B["gamma_b0"], tg[jj]) and np.array_equal(B["n_b0"], tn[jj])
+    assert B["gamma_b0"][-1] == tg[49]
+    L = dict(L)
+    L["s_or_a"] = 10.0 ** np.linspace(7.0, 10.0, 30)   # electronic-band Einstein A: natural widths 3e-5..3e-2
+    N = o.apply_broadening(L, [1.0], gamma_ref=[L["gamma_ref"]], n_t=[L["n_t"]], natural=True)
+    nat = np.asarray(L["s_or_a"], dtype=np.float64) / (4 * math.pi * C["c_m_s"] * 100.0)
+    assert np.allclose(o.lorentz_width_broadened(N, 0.0, 1000.0), nat, rtol=1e-15, atol=0)   # P = 0: natural only
+    assert np.allclose(o.lorentz_width_broadened(N, 2.0, 1000.0) - o.lorentz_width(L["gamma_ref"], L["n_t"], 2.0,
+                       1000.0), nat, rtol=1e-9, atol=1e-300)
+
+
 PINS = [pin_c2, pin_hitran_at_tref, pin_exomol_from_oscillator_strength, pin_hitran_exomol_consistency,
         pin_partition_table, pin_doppler_published, pin_lorentz_closed_forms, pin_voigt_gaussian_limit,
         pin_voigt_centre_erfcx, pin_voigt_lorentz_limit, pin_voigt_convolution_quadrature,
         pin_voigt_scipy_profile, pin_voigt_normalisation, pin_brute_equals_windowed, pin_single_line,
         pin_linearity_and_permutation, pin_grid_shift, pin_cutoff_inclusive, pin_count_evals_bruteforce,
         pin_points_equal_full, pin_nodes_uniform_equals_windowed, pin_nodes_bruteforce, pin_node_windows,
-        pin_fixed_resolution, pin_select_rules, pin_select_sum]
+        pin_fixed_resolution, pin_select_rules, pin_select_sum, pin_broadening_single_equals_power_law,
+        pin_broadening_mixture, pin_broadening_table_and_natural]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -431,3 +472,15 @@ def test_mutation_select_threshold_inverted(monkeypatch):
     real = orc.select_mask
     monkeypatch.setattr(orc, "select_mask", lambda nu0, S, rel, b, og, nb: ~real(nu0, S, rel, b, og, nb))
     assert _fails(pin_select_rules)
+
+
+def test_mutation_natural_width_fwhm(monkeypatch):
+    real = orc.lorentz_width_broadened
+
+    def wrong(lines, P, T):   # natural term as a full width (A / (2 pi c)) instead of the half width
+        g = real(lines, P, T)
+        if lines["natural"]:
+            g = g + np.asarray(lines["s_or_a"], dtype=np.float64) / (4.0 * np.pi * orc.C_LIGHT_CM)
+        return g
+    monkeypatch.setattr(orc, "lorentz_width_broadened", wrong)
+    assert _fails(pin_broadening_table_and_natural)
