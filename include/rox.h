@@ -190,6 +190,46 @@ int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double 
              double Q_T, double Q_ref, double mass_amu, double cutoff, float* sigma_out,
              void* ws, size_t ws_bytes, void* stream);
 
+/* a2 pressure-broadening descriptions and natural broadening (paper, "Compute line-strengths
+ * and -widths": various pressure-broadening descriptions are supported):
+ *   gamma_L = sum_b vmr[b] gamma_ref_b (296/T)^n_b (P / 1.01325 bar) + (natural ? A/(4 pi c) : 0)
+ * over n_broadeners broadeners (1..ROX_MAX_BROADENERS), each with per-line columns
+ * gamma_ref[b], n_t[b] (DEVICE, float or half as lines->width_dtype) or, where table_gamma[b]
+ * is not NULL, values looked up by the line's lower-state J in table_gamma[b][J],
+ * table_n[b][J] (DEVICE float, table_len entries; J < 0 takes entry 0, J >= table_len the
+ * last one; j_lower [n] int32 DEVICE). natural = 1 adds the Lorentz half-width of the
+ * Einstein-A decay, A/(4 pi c) with c in cm/s (ExoMol lists only: s_or_a is A). The list's own
+ * gamma_ref / n_t are not used. */
+#define ROX_MAX_BROADENERS 4
+typedef struct rox_broadening {
+  int32_t n_broadeners;
+  int32_t natural;
+  double vmr[ROX_MAX_BROADENERS];
+  const void* gamma_ref[ROX_MAX_BROADENERS];
+  const void* n_t[ROX_MAX_BROADENERS];
+  const float* table_gamma[ROX_MAX_BROADENERS];
+  const float* table_n[ROX_MAX_BROADENERS];
+  const int32_t* j_lower;
+  int64_t table_len;
+} rox_broadening;
+
+/* gamma_L of every line under `br` at (P_bar, T): gamma_L_out [n] float (device). FP32
+ * arithmetic (each power as exp2 of n_b log2(296/T)). */
+int rox_lorentz_widths(const rox_lines* lines, const rox_broadening* br, double P_bar, double T,
+                       float* gamma_L_out, void* stream);
+
+/* rox_xsec_batch with the Lorentz widths of `br`. Per distinct temperature the broadeners' sum
+ * sum_b vmr_b gamma_ref_b (296/T)^n_b is computed once per line (FP32, kept in the workspace)
+ * and, with natural broadening, A/(4 pi c) once per line; the Voigt kernel then takes
+ * gamma_L = that sum * P/P_ref + the natural width. Arguments otherwise as rox_xsec_batch (the
+ * list's gamma_ref / n_t may be NULL). ws: rox_xsec_broadened_workspace_size(lines->n, grid,
+ * n_temps) bytes. */
+size_t rox_xsec_broadened_workspace_size(int64_t n_lines, const rox_grid* grid, int n_temps);
+int rox_xsec_broadened_batch(const rox_lines* lines, const rox_grid* grid, const rox_broadening* br,
+                             int n_pt, const double* P_bar, const double* T, const double* Q_T,
+                             double Q_ref, double mass_amu, double cutoff, unsigned flags,
+                             float* sigma_out, void* ws, size_t ws_bytes, void* stream);
+
 /* a4/a5 with main-contributor line selection (paper, "Compute line-strengths and -widths": the
  * line-profile step can be sped up by keeping only the main line-strength contributors).
  * At each (P,T) point, with S = S(T) in double precision, the lines are binned by nu0 into

@@ -50,6 +50,17 @@ class RoxSelect(ctypes.Structure):
     _fields_ = [("rel", ctypes.c_double), ("bin_width", ctypes.c_double)]
 
 
+ROX_MAX_BROADENERS = 4
+
+
+class RoxBroadening(ctypes.Structure):
+    _fields_ = [("n_broadeners", ctypes.c_int32), ("natural", ctypes.c_int32),
+                ("vmr", ctypes.c_double * ROX_MAX_BROADENERS), ("gamma_ref", ctypes.c_void_p * ROX_MAX_BROADENERS),
+                ("n_t", ctypes.c_void_p * ROX_MAX_BROADENERS), ("table_gamma", ctypes.c_void_p * ROX_MAX_BROADENERS),
+                ("table_n", ctypes.c_void_p * ROX_MAX_BROADENERS), ("j_lower", ctypes.c_void_p),
+                ("table_len", ctypes.c_int64)]
+
+
 class RoxPrepared(ctypes.Structure):
     _fields_ = [("lines", RoxLines), ("lattice", RoxGrid), ("cutoff", ctypes.c_double), ("state", ctypes.c_void_p),
                 ("span_lo", ctypes.c_void_p), ("span_hi", ctypes.c_void_p), ("n_spans", ctypes.c_int64)]
@@ -95,6 +106,10 @@ def _load():
         "rox_xsec_select_batch": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P, P, ctypes.c_size_t,
                                                  P]),
         "rox_line_select": (ctypes.c_int, [P, P, D, D, D, D, P, P, P, ctypes.c_size_t, P]),
+        "rox_lorentz_widths": (ctypes.c_int, [P, P, D, D, P, P]),
+        "rox_xsec_broadened_workspace_size": (ctypes.c_size_t, [I64, P, ctypes.c_int]),
+        "rox_xsec_broadened_batch": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P,
+                                                    ctypes.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +270,55 @@ def rox_line_select(lines, grid, cutoff, T, Q_T, Q_ref, rel, bin_width, keep_out
     S = RoxSelect(float(rel), float(bin_width))
     _check(lib.rox_line_select(ctypes.byref(L), ctypes.byref(G), cutoff, T, Q_T, Q_ref, ctypes.byref(S),
                                _ptr(keep_out), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def broadening_struct(br):
+    """rox_broadening from a dict: vmr (list), and per broadener either gamma_ref / n_t (lists of
+    CUDA tensors, dtype of the list's widths) or table_gamma / table_n (lists of float32 CUDA tensors)
+    with j_lower (int32 CUDA tensor); natural (bool)."""
+    vmr = list(br["vmr"])
+    nb = len(vmr)
+    B = RoxBroadening()
+    B.n_broadeners = nb
+    B.natural = 1 if br.get("natural") else 0
+    tabs = list(br.get("table_gamma") or [None] * nb) + [None] * nb
+    tabn = list(br.get("table_n") or [None] * nb) + [None] * nb
+    gref = list(br.get("gamma_ref") or [None] * nb) + [None] * nb
+    nts = list(br.get("n_t") or [None] * nb) + [None] * nb
+    for k in range(min(nb, ROX_MAX_BROADENERS)):     # the library rejects more than ROX_MAX_BROADENERS
+        B.vmr[k] = float(vmr[k])
+        B.gamma_ref[k] = _ptr(gref[k]).value if gref[k] is not None else None
+        B.n_t[k] = _ptr(nts[k]).value if nts[k] is not None else None
+        B.table_gamma[k] = _ptr(tabs[k]).value if tabs[k] is not None else None
+        B.table_n[k] = _ptr(tabn[k]).value if tabn[k] is not None else None
+    tl = [t.numel() for t in tabs if t is not None]
+    B.table_len = tl[0] if tl else 0
+    B.j_lower = _ptr(br["j_lower"]).value if br.get("j_lower") is not None else None
+    return B
+
+
+def rox_lorentz_widths(lines, br, P_bar, T, gamma_L_out, stream=None):
+    L = lines_struct(lines)
+    B = broadening_struct(br)
+    _check(lib.rox_lorentz_widths(ctypes.byref(L), ctypes.byref(B), P_bar, T, _ptr(gamma_L_out), _stream(stream)))
+
+
+def rox_xsec_broadened_workspace_size(n_lines, grid, n_temps):
+    G = grid_struct(grid)
+    return lib.rox_xsec_broadened_workspace_size(n_lines, ctypes.byref(G), n_temps)
+
+
+def rox_xsec_broadened_batch(lines, grid, br, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, flags=0,
+                             stream=None):
+    """rox_xsec_batch with the Lorentz widths of the broadening description `br` (see broadening_struct)."""
+    n_pt = len(P_bar)
+    arr = ctypes.c_double * n_pt
+    L = lines_struct(lines)
+    G = grid_struct(grid)
+    B = broadening_struct(br)
+    _check(lib.rox_xsec_broadened_batch(ctypes.byref(L), ctypes.byref(G), ctypes.byref(B), n_pt, arr(*P_bar), arr(*T),
+                                        arr(*Q_T), Q_ref, mass_amu, cutoff, flags, _ptr(sigma_out), _ptr(ws),
+                                        ws.numel(), _stream(stream)))
 
 
 def rox_xsec(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, stream=None):

@@ -43,6 +43,10 @@ cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes);
 cudaError_t rox_launch_select(const double* nu0, const double* S_T, long long n, int n_temps,
                               const unsigned long long* smax_bits, double origin, double width, long long n_bins,
                               double rel, int32_t* bin, unsigned long long* binmax_bits, float* S32, cudaStream_t s);
+cudaError_t rox_launch_broad_T(const RoxBroadDev& B, const float* a_coef, long long n, int n_temps,
+                               const double* temps, float* G, float* gN, cudaStream_t s);
+cudaError_t rox_launch_lorentz_out(const RoxBroadDev& B, const float* a_coef, long long n, double P_bar, double T,
+                                   float* out, cudaStream_t s);
 cudaError_t rox_launch_keep_flags(const double* S_T, const int32_t* bin, const unsigned long long* binmax_bits,
                                   long long n, double rel, uint8_t* keep, cudaStream_t s);
 cudaError_t rox_launch_faddeeva(const float* x, const float* y, float* out, long long n, cudaStream_t s);
@@ -131,11 +135,13 @@ struct WsLayout {
   float2* span_base;
   int32_t* line_bin;   // main-contributor selection only: [n_lines] bins, [n_temps][n_bins] maxima
   unsigned long long* binmax;
+  float* broad_G;      // broadening descriptions only: [n_temps][n_lines] broadeners' sums, [n_lines]
+  float* broad_N;      //   natural widths
   size_t bytes;
 };
 
 WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, bool nodes = false,
-                   long long n_bins = 0) {
+                   long long n_bins = 0, bool broad = false) {
   WsLayout w;
   char* base = (char*)ws;
   size_t off = 0;
@@ -172,8 +178,56 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, b
     w.binmax = (unsigned long long*)(base + off);
     off += rox_align256((size_t)n_temps * (size_t)n_bins * 8);
   }
+  w.broad_G = nullptr;
+  w.broad_N = nullptr;
+  if (broad) {
+    const size_t nl = (size_t)(n_lines > 0 ? n_lines : 1);
+    w.broad_G = (float*)(base + off);
+    off += rox_align256((size_t)n_temps * nl * 4);
+    w.broad_N = (float*)(base + off);
+    off += rox_align256(nl * 4);
+  }
   w.bytes = off;
   return w;
+}
+
+// a rox_broadening checked and put in kernel form
+int check_broadening(const rox_broadening* br, const rox_lines* L, RoxBroadDev* out) {
+  if (!br) return fail(ROX_EINVAL, "broadening is NULL");
+  if (br->n_broadeners < 1 || br->n_broadeners > ROX_MAX_BROADENERS)
+    return fail(ROX_EINVAL, "n_broadeners = %d outside [1, %d]", br->n_broadeners, ROX_MAX_BROADENERS);
+  if (br->natural && L->convention != ROX_EXOMOL)
+    return fail(ROX_EINVAL, "natural broadening needs Einstein A (ExoMol lists)");
+  if (br->natural && L->n > 0 && !L->s_or_a) return fail(ROX_EINVAL, "natural broadening needs lines->s_or_a");
+  bool tables = false;
+  RoxBroadDev B;
+  memset(&B, 0, sizeof B);
+  B.n_b = br->n_broadeners;
+  B.natural = br->natural ? 1 : 0;
+  B.f16 = L->width_dtype == ROX_WIDTH_F16;
+  for (int b = 0; b < br->n_broadeners; b++) {
+    if (!std::isfinite(br->vmr[b]) || br->vmr[b] < 0.0) return fail(ROX_EINVAL, "broadener %d: vmr must be >= 0", b);
+    B.vmr[b] = (float)br->vmr[b];
+    if (br->table_gamma[b]) {
+      if (!br->table_n[b]) return fail(ROX_EINVAL, "broadener %d: table_n is NULL", b);
+      tables = true;
+      B.tab_gamma[b] = br->table_gamma[b];
+      B.tab_n[b] = br->table_n[b];
+    } else {
+      if (L->n > 0 && (!br->gamma_ref[b] || !br->n_t[b]))
+        return fail(ROX_EINVAL, "broadener %d: gamma_ref / n_t columns or a table required", b);
+      B.gamma[b] = br->gamma_ref[b];
+      B.n[b] = br->n_t[b];
+    }
+  }
+  if (tables) {
+    if (br->table_len < 1) return fail(ROX_EINVAL, "table_len must be >= 1");
+    if (L->n > 0 && !br->j_lower) return fail(ROX_EINVAL, "j_lower is required with tables");
+    B.j_lower = br->j_lower;
+    B.tab_len = br->table_len;
+  }
+  *out = B;
+  return ROX_OK;
 }
 
 // main-contributor selection bins of a uniform grid: origin nu_min - cutoff, width B
@@ -343,8 +397,11 @@ namespace {
 int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_nodes* nodes, int n_pt,
                     const double* P_bar, const double* T, const double* Q_T, double Q_ref, double mass_amu,
                     double cutoff, unsigned flags, float* sigma_out, void* ws, size_t ws_bytes, void* stream,
-                    const rox_select* sel = nullptr) {
-  int rc = check_lines(lines, true, true);
+                    const rox_select* sel = nullptr, const rox_broadening* br = nullptr) {
+  int rc = check_lines(lines, true, br == nullptr);
+  if (rc) return rc;
+  RoxBroadDev bdev;
+  if (br && (rc = check_broadening(br, lines, &bdev))) return rc;
   if (rc) return rc;
   const bool on_nodes = nodes != nullptr;
   double sel_origin = 0.0;
@@ -376,7 +433,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   }
   const int n_temps = (int)temps.size();
   if (!ws || ((uintptr_t)ws & 255)) return fail(ROX_EINVAL, "workspace NULL or not 256-byte aligned");
-  WsLayout w = ws_layout(ws, lines->n, n_grid, n_temps, on_nodes, n_bins);
+  WsLayout w = ws_layout(ws, lines->n, n_grid, n_temps, on_nodes, n_bins, br != nullptr);
   if (ws_bytes < w.bytes) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.bytes);
 
   cudaStream_t s = (cudaStream_t)stream;
@@ -407,6 +464,10 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
                                 sel->rel, w.line_bin, w.binmax, w.S32, s)
             : rox_launch_scale_strengths(w.S_T, nl, n_temps, w.hdr->smax_bits, w.S32, s);
     if ((rc = cuda_check(se, "strength scaling kernel"))) return rc;
+    if (br && (rc = cuda_check(rox_launch_broad_T(bdev, lines->s_or_a, nl, n_temps, temps.data(), w.broad_G,
+                                                  bdev.natural ? w.broad_N : nullptr, s),
+                               "broadening kernel")))
+      return rc;
   }
   if ((rc = cuda_check(rox_launch_tile_ranges_geo(w.geo, nl, nt, ROX_TILE, w.tlo, w.thi, s), "tile ranges")))
     return rc;
@@ -417,6 +478,9 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   L0.span_hi = w.thi;
   L0.gamma_ref = lines->gamma_ref;
   L0.n_t = lines->n_t;
+  L0.gLT = br ? w.broad_G : nullptr;
+  L0.gLT_stride = nl > 0 ? nl : 1;
+  L0.gN = (br && bdev.natural) ? w.broad_N : nullptr;
   L0.node_d = w.node_d;
   L0.span_base = w.span_base;
   L0.n_lattice = n_grid;
@@ -441,7 +505,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
     J.gG_fac = (float)(sqrt(2.0 * ROX_KB * T[k] / (mass_amu * ROX_AMU)) / ROX_C_M);
     J.l2_ratio = (float)log2(ROX_T_REF / T[k]);
     J.flags = flags;
-    J.pad = 0;
+    J.t_row = tidx[k];
   }
   if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, w.tail_part, w.tail_cnt, w.tail_cap, nblocks, s,
                               on_nodes)))
@@ -460,6 +524,39 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt, const
   if ((rc = check_cutoff(cutoff, grid))) return rc;
   return xsec_batch_impl(lines, grid, nullptr, n_pt, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, flags, sigma_out, ws,
                          ws_bytes, stream);
+}
+
+size_t rox_xsec_broadened_workspace_size(int64_t n_lines, const rox_grid* grid, int n_temps) {
+  if (!grid || grid->n <= 0 || n_lines < 0 || n_temps <= 0) return 0;
+  return ws_layout(nullptr, n_lines, grid->n, n_temps, false, 0, true).bytes;
+}
+
+int rox_xsec_broadened_batch(const rox_lines* lines, const rox_grid* grid, const rox_broadening* br, int n_pt,
+                             const double* P_bar, const double* T, const double* Q_T, double Q_ref, double mass_amu,
+                             double cutoff, unsigned flags, float* sigma_out, void* ws, size_t ws_bytes,
+                             void* stream) {
+  int rc;
+  if ((rc = check_grid(grid))) return rc;
+  if ((rc = check_cutoff(cutoff, grid))) return rc;
+  if (!br) return fail(ROX_EINVAL, "broadening is NULL");
+  return xsec_batch_impl(lines, grid, nullptr, n_pt, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, flags, sigma_out, ws,
+                         ws_bytes, stream, nullptr, br);
+}
+
+int rox_lorentz_widths(const rox_lines* lines, const rox_broadening* br, double P_bar, double T, float* gamma_L_out,
+                       void* stream) {
+  int rc = check_lines(lines, false, false);
+  if (rc) return rc;
+  RoxBroadDev B;
+  if ((rc = check_broadening(br, lines, &B))) return rc;
+  if (!finite_pos(T) || !std::isfinite(P_bar) || P_bar < 0) return fail(ROX_EINVAL, "T > 0 and P >= 0 required");
+  if (!gamma_L_out) return fail(ROX_EINVAL, "gamma_L_out is NULL");
+  if (lines->n == 0) return ok();
+  if ((rc = cuda_check(rox_launch_lorentz_out(B, lines->s_or_a, lines->n, P_bar, T, gamma_L_out,
+                                              (cudaStream_t)stream),
+                       "Lorentz widths kernel")))
+    return rc;
+  return ok();
 }
 
 size_t rox_xsec_select_workspace_size(int64_t n_lines, const rox_grid* grid, int n_temps, double cutoff,
@@ -725,6 +822,9 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     L[l].span_hi = (const long long*)P.span_hi;
     L[l].gamma_ref = P.lines.gamma_ref;
     L[l].n_t = P.lines.n_t;
+    L[l].gLT = nullptr;
+    L[l].gLT_stride = 0;
+    L[l].gN = nullptr;
     L[l].node_d = nullptr;
     L[l].span_base = nullptr;
     L[l].n_lattice = P.lattice.n;
@@ -751,7 +851,7 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     d.gG_fac = (float)(sqrt(2.0 * ROX_KB * j.T / (j.mass_amu * ROX_AMU)) / ROX_C_M);
     d.l2_ratio = (float)log2(ROX_T_REF / j.T);
     d.flags = j.flags;
-    d.pad = 0;
+    d.t_row = 0;
   }
   if ((rc = launch_voigt_jobs(L, n_lists, J.data(), n_jobs, hdr, tail.part, tail.cnt, tail.cap, nblocks, s)))
     return rc;

@@ -54,6 +54,12 @@ struct RoxListDev {
   const long long* span_hi;   //   and one past the last
   const void* gamma_ref;
   const void* n_t;
+  // broadened lists only (else NULL): per line and distinct temperature the broadeners' sum
+  // sum_b vmr_b gamma_ref_b (296/T)^n_b, the job's row at gLT + t_row * gLT_stride; per line
+  // the natural width (or NULL)
+  const float* gLT;
+  long long gLT_stride;
+  const float* gN;
   // user-provided nodes only (NULL on a uniform grid): per node its offset from the first node
   // of its span, per span that first node, both as double-float pairs {hi, lo}; geo then holds
   // {nu0 hi, nu0 lo, jlo, jhi}
@@ -64,6 +70,21 @@ struct RoxListDev {
   float nu_min_f;
   int32_t width_f16;
   int32_t pad;
+};
+
+// Lorentz-width description of rox_broadening in kernel parameter form
+struct RoxBroadDev {
+  int32_t n_b;
+  int32_t natural;
+  int32_t f16;                 // per-line columns stored as half
+  int32_t pad;
+  float vmr[ROX_MAX_BROADENERS];
+  const void* gamma[ROX_MAX_BROADENERS];
+  const void* n[ROX_MAX_BROADENERS];
+  const float* tab_gamma[ROX_MAX_BROADENERS];
+  const float* tab_n[ROX_MAX_BROADENERS];
+  const int32_t* j_lower;
+  long long tab_len;
 };
 
 struct RoxJobDev {
@@ -81,7 +102,7 @@ struct RoxJobDev {
   float gG_fac;     // sqrt(2 k T / (m amu)) / c  -> gamma_G = nu0 * gG_fac
   float l2_ratio;   // log2(T_ref / T)           -> (T_ref/T)^n_T = exp2(n_T * l2_ratio)
   uint32_t flags;   // ROX_ACCUMULATE
-  uint32_t pad;
+  int32_t t_row;    // broadened lists: the job's temperature row of the list's gLT
 };
 
 // Every span's lines are summed as ROX_PARTS consecutive parts (batch-aligned), each from

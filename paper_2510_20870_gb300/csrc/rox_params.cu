@@ -107,6 +107,54 @@ __global__ void k_scale_strengths(const double* __restrict__ S_T, long long n, i
   }
 }
 
+// ---- a2 broadening descriptions: sum_b vmr_b gamma_b (296/T)^n_b of line i, l2 = log2(296/T)
+__device__ __forceinline__ float broad_col(const void* p, int f16, long long i) {
+  return f16 ? __half2float(reinterpret_cast<const __half*>(p)[i]) : reinterpret_cast<const float*>(p)[i];
+}
+__device__ __forceinline__ float broad_sum(const RoxBroadDev& B, long long i, float l2) {
+  long long j = 0;
+  if (B.j_lower) {
+    j = B.j_lower[i];
+    j = j < 0 ? 0 : (j >= B.tab_len ? B.tab_len - 1 : j);
+  }
+  float g = 0.0f;
+  for (int b = 0; b < B.n_b; b++) {
+    float gb, nb;
+    if (B.tab_gamma[b]) {
+      gb = B.tab_gamma[b][j];
+      nb = B.tab_n[b][j];
+    } else {
+      gb = broad_col(B.gamma[b], B.f16, i);
+      nb = broad_col(B.n[b], B.f16, i);
+    }
+    g = fmaf(B.vmr[b] * gb, exp2f(nb * l2), g);
+  }
+  return g;
+}
+#define ROX_INV_4PI_C 2.6544187294380724e-12f   // 1 / (4 pi c), c in cm/s
+
+struct BroadTemps {
+  int32_t n;
+  float l2[ROX_MAX_PT];
+};
+
+// per distinct temperature the broadeners' sum of every line (G[t][i]); natural widths once
+__global__ void k_broad_T(RoxBroadDev B, const float* __restrict__ a_coef, long long n, BroadTemps ts, float* G,
+                          float* gN) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (int t = 0; t < ts.n; t++) G[(long long)t * n + i] = broad_sum(B, i, ts.l2[t]);
+    if (gN) gN[i] = a_coef[i] * ROX_INV_4PI_C;
+  }
+}
+
+__global__ void k_lorentz_out(RoxBroadDev B, const float* __restrict__ a_coef, long long n, float l2, float p_fac,
+                              float* out) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = fmaf(broad_sum(B, i, l2), p_fac, B.natural ? a_coef[i] * ROX_INV_4PI_C : 0.0f);
+}
+
 // Main-contributor selection, bin of every line: floor((nu0 - origin) / width) with the
 // subtraction and the division each rounded once in double precision; -1 outside [0, n_bins).
 __global__ void k_line_bins(const double* __restrict__ nu0, long long n, double origin, double width,
@@ -271,6 +319,22 @@ cudaError_t rox_launch_select(const double* nu0, const double* S_T, long long n,
   k_line_bins<<<grid_for(n), 256, 0, s>>>(nu0, n, origin, width, n_bins, bin);
   k_bin_max<<<grid_for((n + ROX_BIN_RUN - 1) / ROX_BIN_RUN), 256, 0, s>>>(bin, S_T, n, n_temps, n_bins, binmax_bits);
   k_scale_strengths<<<grid_for(n), 256, 0, s>>>(S_T, n, n_temps, smax_bits, S32, bin, binmax_bits, n_bins, rel);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_broad_T(const RoxBroadDev& B, const float* a_coef, long long n, int n_temps,
+                               const double* temps, float* G, float* gN, cudaStream_t s) {
+  BroadTemps ts;
+  ts.n = n_temps;
+  for (int t = 0; t < n_temps; t++) ts.l2[t] = (float)log2(ROX_T_REF / temps[t]);
+  k_broad_T<<<grid_for(n), 256, 0, s>>>(B, a_coef, n, ts, G, gN);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_lorentz_out(const RoxBroadDev& B, const float* a_coef, long long n, double P_bar, double T,
+                                   float* out, cudaStream_t s) {
+  k_lorentz_out<<<grid_for(n), 256, 0, s>>>(B, a_coef, n, (float)log2(ROX_T_REF / T), (float)(P_bar / ROX_P_REF),
+                                            out);
   return cudaGetLastError();
 }
 

@@ -65,6 +65,19 @@ __device__ __forceinline__ float load_width(const void* p, int f16, long long i)
              : reinterpret_cast<const float*>(p)[i];
 }
 
+// the two per-line width inputs of line i: {gamma_ref, n_T} of the single power law, or, for
+// broadened lists, {the broadeners' sum at the job's temperature, the natural width}
+__device__ __forceinline__ void load_widths(const RoxJobDev& J, const RoxListDev& L, int f16, long long i, float& a,
+                                            float& b) {
+  if (L.gLT) {
+    a = L.gLT[(long long)J.t_row * L.gLT_stride + i];
+    b = L.gN ? L.gN[i] : 0.0f;
+  } else {
+    a = load_width(L.gamma_ref, f16, i);
+    b = load_width(L.n_t, f16, i);
+  }
+}
+
 // one point of one line outside the slow zone: S V = n / d
 __device__ __forceinline__ float far_term(float X, const float4& a, const float4& b) {
   float t = fmaf(X, X, a.z);
@@ -299,8 +312,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
       if (plo + lane < phi) {
         cp_async16(&geo_st[0][lane], &Lst.geo[plo + lane]);
         cp_async4(&S_st[0][lane], &S_row[plo + lane]);
-        gref = load_width(Lst.gamma_ref, f16, plo + lane);
-        nt = load_width(Lst.n_t, f16, plo + lane);
+        load_widths(J, Lst, f16, plo + lane, gref, nt);
       }
       cp_async_commit();
       int nb = 0;
@@ -311,8 +323,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         if (b0 + 32 + lane < phi) {
           cp_async16(&geo_st[buf ^ 1][lane], &Lst.geo[b0 + 32 + lane]);
           cp_async4(&S_st[buf ^ 1][lane], &S_row[b0 + 32 + lane]);
-          gref_n = load_width(Lst.gamma_ref, f16, b0 + 32 + lane);
-          nt_n = load_width(Lst.n_t, f16, b0 + 32 + lane);
+          load_widths(J, Lst, f16, b0 + 32 + lane, gref_n, nt_n);
         }
         cp_async_commit();
         cp_async_wait1();   // this lane's copies of the current batch have landed
@@ -337,7 +348,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             ay = g.y;
           }
           const float gG = nu0f * J.gG_fac;
-          const float gL = gref * exp2f(nt * J.l2_ratio) * J.p_fac;
+          const float gL = Lst.gLT ? fmaf(gref, J.p_fac, nt) : gref * exp2f(nt * J.l2_ratio) * J.p_fac;
           has_S = Sp != 0.0f;
           const bool dropped = __float_as_uint(Sp) == 0x80000000u;   // -0.0: not kept by a selection
           const long long ov = min((long long)jhi, whi) - max((long long)jlo, wlo) + 1;

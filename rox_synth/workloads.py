@@ -226,3 +226,11 @@ def irregular_nodes(seed: int, lo: float, hi: float, n: int):
     clus = centres[(np.arange(n - n // 2) % 8)] + width * (u[n:n + n - n // 2] - 0.5)
     nodes = np.unique(np.clip(np.concatenate([base, clus]), lo, hi))
     return nodes.astype(np.float64)
+
+
+def j_lower_of(w: Workload, start: int = 0, count: int = None):
+    """Lower-state rotational quantum number J'' of lines start..start+count-1 (int32, uniform
+    0..99; Philox stream 41), the key of J-dependent broadening tables."""
+    if count is None:
+        count = w.n_lines - start
+    return np.floor(100.0 * uniform01(w.seed, 41, start, count)).astype(np.int32)
