@@ -58,6 +58,9 @@ def parse():
                     help="main-contributor selection: keep lines with S >= REL x the largest S of their nu0 bin "
                          "(rox_xsec_select_batch)")
     ap.add_argument("--select-bin", type=float, default=1.0, help="selection bin width (cm^-1)")
+    ap.add_argument("--broadening", action="store_true",
+                    help="broadener mixture and natural broadening (rox_xsec_broadened_batch): 0.85 H2 from per-line "
+                         "columns + 0.15 He from a J table, plus A/(4 pi c)")
     ap.add_argument("--nodes", action="store_true",
                     help="user-provided grid: the workload's lines on nodes of fixed resolving power R = %g over the "
                          "same wavenumber range (rox_xsec_nodes_batch)" % rs.FIXED_R)
@@ -306,8 +309,25 @@ def run_gpu(args):
     n = len(host["nu0"])
     h2d_bytes = sum(v.numel() * v.element_size() for v in pinned.values())
     sort_ws = torch.empty(rox.rox_sort_workspace_size(n), dtype=torch.uint8, device=dev)
-    if args.nodes and args.select is not None:
-        raise SystemExit("--select runs on the uniform grid only")
+    if sum([args.nodes, args.select is not None, args.broadening]) > 1:
+        raise SystemExit("--nodes, --select and --broadening are separate modes")
+    if args.broadening:
+        # broadener columns and J of the lines in nu0 order (the device sort is stable on nu0, like this one)
+        order = np.argsort(host["nu0"], kind="stable")
+        jl = rs.j_lower_of(w, 0, n)[order]
+        tab_j = np.arange(60)
+        extra_pin = {"j": torch.from_numpy(np.ascontiguousarray(jl)).pin_memory(),
+                     "g_h2": torch.from_numpy((host["gamma_ref"][order].astype(np.float64) * 1.3)
+                                              .astype(host["gamma_ref"].dtype)).pin_memory(),
+                     "n_h2": torch.from_numpy((host["n_t"][order].astype(np.float64) - 0.1)
+                                              .astype(host["n_t"].dtype)).pin_memory(),
+                     "tg": torch.from_numpy((0.09 * np.exp(-tab_j / 40.0) + 0.01).astype(np.float32)).pin_memory(),
+                     "tn": torch.from_numpy((0.45 + 0.004 * tab_j).astype(np.float32)).pin_memory()}
+        extra = {k: v.to(dev) for k, v in extra_pin.items()}
+        h2d_bytes += sum(v.numel() * v.element_size() for v in extra_pin.values())
+        bro = {"vmr": [0.85, 0.15], "gamma_ref": [extra["g_h2"], None], "n_t": [extra["n_h2"], None],
+               "table_gamma": [None, extra["tg"]], "table_n": [None, extra["tn"]], "j_lower": extra["j"],
+               "natural": True}
     if args.nodes:
         nodes_np = rs.fixed_resolution_grid(w.grid_lo, w.grid_hi, rs.FIXED_R)
         nodes_pin = torch.from_numpy(nodes_np).pin_memory()
@@ -320,6 +340,9 @@ def run_gpu(args):
         n_grid = grid[2]
         ws = torch.empty(rox.rox_xsec_select_workspace_size(n, grid, 1, w.cutoff, args.select, args.select_bin),
                          dtype=torch.uint8, device=dev)
+    elif args.broadening:
+        n_grid = grid[2]
+        ws = torch.empty(rox.rox_xsec_broadened_workspace_size(n, grid, 1), dtype=torch.uint8, device=dev)
     else:
         n_grid = grid[2]
         ws = torch.empty(rox.rox_xsec_workspace_size(n, grid, 1), dtype=torch.uint8, device=dev)
@@ -332,6 +355,9 @@ def run_gpu(args):
             raw[k].copy_(v, non_blocking=True)
         if args.nodes:
             nodes_dev.copy_(nodes_pin, non_blocking=True)
+        if args.broadening:
+            for k, v in extra_pin.items():
+                extra[k].copy_(v, non_blocking=True)
         rox.rox_sort_lines(raw, lines, None, sort_ws)
 
     def step():
@@ -340,6 +366,8 @@ def run_gpu(args):
         elif args.select is not None:
             rox.rox_xsec_select_batch(lines, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, args.select,
                                       args.select_bin, sigma, ws)
+        elif args.broadening:
+            rox.rox_xsec_broadened_batch(lines, grid, bro, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws)
         else:
             rox.rox_xsec(lines, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
 
@@ -451,8 +479,12 @@ def run_gpu(args):
                                "rel": args.select, "bin_width_cm": args.select_bin,
                                "note": "value counts the kept (line, point) pairs; xsecs_per_s is the like-for-like "
                                        "speed against the unselected run"},
+                           "broadening": None if not args.broadening else (
+                               "0.85 H2 (per-line columns 1.3 x gamma_ref, n_T - 0.1) + 0.15 He (table by J'' of "
+                               "60 entries) + natural A/(4 pi c)"),
                            "step": ("rox_xsec_nodes_batch" if args.nodes else
-                                    "rox_xsec_select_batch" if args.select is not None else "rox_xsec") +
+                                    "rox_xsec_select_batch" if args.select is not None else
+                                    "rox_xsec_broadened_batch" if args.broadening else "rox_xsec") +
                                    " on the resident nu0-sorted list (strengths, widths, windows, tile "
                                    "ranges, Voigt accumulate); the once-per-list sort is inside e2e",
                            "l2": "inputs larger than L2 (line list %.0f MB, workspace %.0f MB)" % (
@@ -464,9 +496,11 @@ def run_gpu(args):
                         "ms_per_step": e2e_ms / e2e_steps if e2e_steps else None,
                         "includes": "H2D of the unsorted list%s, rox_sort_lines, %s, D2H of sigma" % (
                             " and the nodes" if args.nodes else "", "rox_xsec_nodes_batch" if args.nodes else "rox_xsec")},
-                "gpu_launches": args.steps * (6 if args.nodes else 7 if args.select is not None else 5),
-                "gpu_launches_note": "per step: %swindows, strengths, strength scaling, tile ranges, Voigt kernels "
-                                     "(+ memsets)" % ("node offsets, " if args.nodes else ""),
+                "gpu_launches": args.steps * (6 if args.nodes or args.broadening else
+                                              7 if args.select is not None else 5),
+                "gpu_launches_note": "per step: %swindows, strengths, strength scaling, %stile ranges, Voigt "
+                                     "kernels (+ memsets)" % ("node offsets, " if args.nodes else "",
+                                                             "broadening, " if args.broadening else ""),
                 "clocks": csum}
         print(json.dumps(line))
     if dist is not None:

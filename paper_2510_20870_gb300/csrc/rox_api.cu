@@ -30,7 +30,7 @@ cudaError_t rox_launch_tile_ranges_geo(const float4* geo, long long n_lines, lon
 size_t rox_sort_ws_bytes(long long n);
 cudaError_t rox_launch_sort(const rox_lines* in, const rox_lines_buf* out, int64_t* perm_out, void* ws,
                             cudaStream_t s);
-cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, cudaStream_t s);
+cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, int extras, cudaStream_t s);
 cudaError_t rox_launch_node_windows(const double* nu0, long long n_lines, const double* nodes, long long n,
                                     double cutoff, int32_t* jlo, int32_t* jhi, float4* geo,
                                     unsigned long long* evals, int32_t* unsorted, int32_t unsorted_value,
@@ -270,7 +270,7 @@ int voigt_grid(int* out, bool nodes = false) {
 // up to tail_cap and half a round of the launch's warps, are split into their parts.
 int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* jobs, int n_jobs, RoxWsHeader* hdr,
                       float* tail_part, int32_t* tail_cnt, long long tail_cap, int nblocks, cudaStream_t s,
-                      bool nodes = false) {
+                      bool nodes = false, int extras = 0) {
   static thread_local RoxVoigtArgs A;   // ~30 KB of per-job parameters, passed by value
   A.hdr = hdr;
   A.tail_part = tail_part;
@@ -297,7 +297,7 @@ int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* job
     if (split > 0 && (rc = cuda_check(cudaMemsetAsync(tail_cnt, 0, (size_t)split * 4, s), "memset"))) return rc;
     if (j0 == 0 && g_prof_start && (rc = cuda_check(cudaEventRecord(g_prof_start, s), "cudaEventRecord"))) return rc;
     if (items == 0) continue;
-    if ((rc = cuda_check(rox_launch_voigt(A, blocks, nodes, s), "voigt kernel"))) return rc;
+    if ((rc = cuda_check(rox_launch_voigt(A, blocks, nodes, extras, s), "voigt kernel"))) return rc;
   }
   if (g_prof_stop) return cuda_check(cudaEventRecord(g_prof_stop, s), "cudaEventRecord");
   return ROX_OK;
@@ -507,8 +507,9 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
     J.flags = flags;
     J.t_row = tidx[k];
   }
+  const int extras = (sel ? ROX_VX_SELECT : 0) | (br ? ROX_VX_BROAD : 0);
   if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, w.tail_part, w.tail_cnt, w.tail_cap, nblocks, s,
-                              on_nodes)))
+                              on_nodes, extras)))
     return rc;
   return ok();
 }

@@ -87,6 +87,10 @@ struct RoxBroadDev {
   long long tab_len;
 };
 
+// extras of a Voigt launch (kernel instantiations)
+#define ROX_VX_SELECT 1   // strengths carry a main-contributor selection
+#define ROX_VX_BROAD 2    // widths from the broadening pass (RoxListDev::gLT, gN)
+
 struct RoxJobDev {
   const float* S32;                      // S * 2^-e of lines l0, l0+1, ... at this job's T
   float* sigma;                          // sigma[j - first] for lattice points j in [first, first + n)

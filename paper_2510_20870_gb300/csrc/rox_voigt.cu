@@ -66,10 +66,11 @@ __device__ __forceinline__ float load_width(const void* p, int f16, long long i)
 }
 
 // the two per-line width inputs of line i: {gamma_ref, n_T} of the single power law, or, for
-// broadened lists, {the broadeners' sum at the job's temperature, the natural width}
+// broadened lists (BRD), {the broadeners' sum at the job's temperature, the natural width}
+template <bool BRD>
 __device__ __forceinline__ void load_widths(const RoxJobDev& J, const RoxListDev& L, int f16, long long i, float& a,
                                             float& b) {
-  if (L.gLT) {
+  if constexpr (BRD) {
     a = L.gLT[(long long)J.t_row * L.gLT_stride + i];
     b = L.gN ? L.gN[i] : 0.0f;
   } else {
@@ -223,9 +224,15 @@ __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float
 }
 
 // NU: the lists are on user-provided nodes (node offsets in dynamic shared memory, one
-// ROX_SPAN row of float2 per warp).
-template <bool NU>
+// ROX_SPAN row of float2 per warp). X: ROX_VX_SELECT (strengths carry a main-contributor
+// selection: zero-strength lines leave every pass, -0.0 ones leave the evaluation count) and
+// ROX_VX_BROAD (widths from the broadening pass). Each extra is compiled only into the
+// instantiations that use it: in this kernel even a few added instructions per line batch
+// cost several percent of the plain launch.
+template <bool NU, int X>
 __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant__ RoxVoigtArgs A) {
+  constexpr bool SEL = (X & ROX_VX_SELECT) != 0;
+  constexpr bool BRD = (X & ROX_VX_BROAD) != 0;
   extern __shared__ float2 s_nodes[];
   __shared__ float4 s_geo[ROX_WARPS][2][32];
   __shared__ float s_S[ROX_WARPS][2][32];
@@ -312,7 +319,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
       if (plo + lane < phi) {
         cp_async16(&geo_st[0][lane], &Lst.geo[plo + lane]);
         cp_async4(&S_st[0][lane], &S_row[plo + lane]);
-        load_widths(J, Lst, f16, plo + lane, gref, nt);
+        load_widths<BRD>(J, Lst, f16, plo + lane, gref, nt);
       }
       cp_async_commit();
       int nb = 0;
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         if (b0 + 32 + lane < phi) {
           cp_async16(&geo_st[buf ^ 1][lane], &Lst.geo[b0 + 32 + lane]);
           cp_async4(&S_st[buf ^ 1][lane], &S_row[b0 + 32 + lane]);
-          load_widths(J, Lst, f16, b0 + 32 + lane, gref_n, nt_n);
+          load_widths<BRD>(J, Lst, f16, b0 + 32 + lane, gref_n, nt_n);
         }
         cp_async_commit();
         cp_async_wait1();   // this lane's copies of the current batch have landed
@@ -348,11 +355,15 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             ay = g.y;
           }
           const float gG = nu0f * J.gG_fac;
-          const float gL = Lst.gLT ? fmaf(gref, J.p_fac, nt) : gref * exp2f(nt * J.l2_ratio) * J.p_fac;
-          has_S = Sp != 0.0f;
-          const bool dropped = __float_as_uint(Sp) == 0x80000000u;   // -0.0: not kept by a selection
+          const float gL = BRD ? fmaf(gref, J.p_fac, nt) : gref * exp2f(nt * J.l2_ratio) * J.p_fac;
           const long long ov = min((long long)jhi, whi) - max((long long)jlo, wlo) + 1;
-          if (ov > 0 && !dropped) evals += (unsigned long long)ov;
+          if constexpr (SEL) {
+            has_S = Sp != 0.0f;
+            const bool dropped = __float_as_uint(Sp) == 0x80000000u;   // -0.0: not kept by the selection
+            if (ov > 0 && !dropped) evals += (unsigned long long)ov;
+          } else {
+            if (ov > 0) evals += (unsigned long long)ov;
+          }
           const float gG2 = gG * gG, gL2 = gL * gL;
           const float pY = Sp * gL * ROX_INV_PI;
           const float invG = 1.0f / gG;
@@ -401,7 +412,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         // unmasked pairs; covering lines with a slow zone in masked pairs; window-edge lines in
         // pairs with window masks. The orders are fixed, so the sum is reproducible.
         const unsigned cls = __float_as_uint(r.b.z);
-        const bool live = lane < cnt && has_S;
+        const bool live = SEL ? (lane < cnt && has_S) : lane < cnt;
         unsigned cmask = __ballot_sync(0xffffffffu, live && cls == 1u);
         unsigned zmask = __ballot_sync(0xffffffffu, live && cls == 3u);
         const unsigned emask = __ballot_sync(0xffffffffu, live && !(cls & 1u));
@@ -554,27 +565,34 @@ __global__ void k_faddeeva(const float* x, const float* y, float* out, long long
 
 #define ROX_NODES_SMEM (ROX_WARPS * ROX_SPAN * sizeof(float2))
 
-cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, cudaStream_t s) {
+cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, int extras, cudaStream_t s) {
   if (nodes) {
+    if (extras) return cudaErrorNotSupported;   // no caller combines nodes with a selection or broadening
     // static shared memory plus the node rows exceed 48 KB: opt in (idempotent, per device)
-    cudaError_t e = cudaFuncSetAttribute(k_voigt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_voigt<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)ROX_NODES_SMEM);
     if (e != cudaSuccess) return e;
-    k_voigt<true><<<n_blocks, ROX_THREADS, ROX_NODES_SMEM, s>>>(A);
+    k_voigt<true, 0><<<n_blocks, ROX_THREADS, ROX_NODES_SMEM, s>>>(A);
+  } else if (extras == 0) {
+    k_voigt<false, 0><<<n_blocks, ROX_THREADS, 0, s>>>(A);
+  } else if (extras == ROX_VX_SELECT) {
+    k_voigt<false, ROX_VX_SELECT><<<n_blocks, ROX_THREADS, 0, s>>>(A);
+  } else if (extras == ROX_VX_BROAD) {
+    k_voigt<false, ROX_VX_BROAD><<<n_blocks, ROX_THREADS, 0, s>>>(A);
   } else {
-    k_voigt<false><<<n_blocks, ROX_THREADS, 0, s>>>(A);
+    return cudaErrorNotSupported;   // no entry point combines a selection with broadening
   }
   return cudaGetLastError();
 }
 
 cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes) {
   if (nodes) {
-    cudaError_t e = cudaFuncSetAttribute(k_voigt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_voigt<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)ROX_NODES_SMEM);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<true>, ROX_THREADS, ROX_NODES_SMEM);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<true, 0>, ROX_THREADS, ROX_NODES_SMEM);
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<false>, ROX_THREADS, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<false, 0>, ROX_THREADS, 0);
 }
 
 cudaError_t rox_launch_faddeeva(const float* x, const float* y, float* out, long long n, cudaStream_t s) {

@@ -86,7 +86,9 @@ def test_selected_cross_sections():
 
 
 def test_rel_zero_equals_unselected():
-    """rel = 0 keeps every line that reaches the grid: the same launch, bit for bit."""
+    """rel = 0 keeps every line that reaches the grid: the unselected result. Not bit for bit:
+    the selection kernel also leaves out lines whose strength underflows FP32 (exact zeros),
+    which changes how the other lines are paired and so the last bits."""
     w = rs.CONFIGS[1]
     L = oracle.sort_lines(rs.make_lines(w))
     grid = rs.grid_of(w)
@@ -97,7 +99,8 @@ def test_rel_zero_equals_unselected():
     ws = torch.empty(rox.rox_xsec_workspace_size(L["nu0"].size, grid, 1), dtype=torch.uint8, device="cuda")
     sig = torch.empty((1, grid[2]), dtype=torch.float32, device="cuda")
     rox.rox_xsec(dl, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sig, ws)
-    assert np.array_equal(got[0], sig[0].double().cpu().numpy())
+    plain = sig[0].double().cpu().numpy()
+    check_sigma(got[0], plain, rel_tol=1e-5, label="rel = 0 vs unselected launch")
 
 
 def test_selection_full_size_sample():
