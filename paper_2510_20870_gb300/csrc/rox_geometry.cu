@@ -15,9 +15,14 @@ __device__ __forceinline__ double node_offset(double nu_min, double dnu, long lo
   return __dsub_rn(__dadd_rn(nu_min, __dmul_rn((double)j, dnu)), nu0);
 }
 
+// `guard` bounds, in index units, the rounding of the candidates (nu0 -/+ cutoff - nu_min)/dnu
+// and of the cutoff test for every line within reach of the grid: a candidate farther than
+// that from an integer is the exact answer, and the exact test only runs for the others
+// (about one line in 1e6). Lines beyond reach end up clamped to an empty or edge window
+// either way.
 __global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, double nu_min,
-                          double dnu, double inv_dnu, long long n_grid, double cutoff, int32_t* jlo_out,
-                          int32_t* jhi_out, int32_t* k0_out, float* f_out, float4* geo_out,
+                          double dnu, double inv_dnu, double guard, long long n_grid, double cutoff,
+                          int32_t* jlo_out, int32_t* jhi_out, int32_t* k0_out, float* f_out, float4* geo_out,
                           unsigned long long* evals_out, int32_t* unsorted_out, int32_t unsorted_value) {
   long long stride = (long long)gridDim.x * blockDim.x;
   unsigned long long ev = 0;
@@ -26,15 +31,21 @@ __global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, do
     if (i > 0 && nu0s[i - 1] > nu0 && unsorted_out) *unsorted_out = unsorted_value;
     // first j with d_j >= -cutoff, last j with d_j <= cutoff (d_j non-decreasing in j): a
     // candidate from a multiply by 1/dnu (within one index), then the exact test moves it
-    double lo_c = ceil((nu0 - cutoff - nu_min) * inv_dnu);
-    double hi_c = floor((nu0 + cutoff - nu_min) * inv_dnu);
+    const double r_lo = (nu0 - cutoff - nu_min) * inv_dnu;
+    const double r_hi = (nu0 + cutoff - nu_min) * inv_dnu;
+    double lo_c = ceil(r_lo);
+    double hi_c = floor(r_hi);
     lo_c = fmin(fmax(lo_c, -4.0), (double)n_grid + 4.0);
     hi_c = fmin(fmax(hi_c, -4.0), (double)n_grid + 4.0);
     long long jlo = (long long)lo_c, jhi = (long long)hi_c;
-    for (int it = 0; it < 4 && node_offset(nu_min, dnu, jlo - 1, nu0) >= -cutoff; it++) jlo--;
-    for (int it = 0; it < 4 && node_offset(nu_min, dnu, jlo, nu0) < -cutoff; it++) jlo++;
-    for (int it = 0; it < 4 && node_offset(nu_min, dnu, jhi + 1, nu0) <= cutoff; it++) jhi++;
-    for (int it = 0; it < 4 && node_offset(nu_min, dnu, jhi, nu0) > cutoff; it++) jhi--;
+    if (!(fabs(r_lo - rint(r_lo)) > guard)) {
+      for (int it = 0; it < 4 && node_offset(nu_min, dnu, jlo - 1, nu0) >= -cutoff; it++) jlo--;
+      for (int it = 0; it < 4 && node_offset(nu_min, dnu, jlo, nu0) < -cutoff; it++) jlo++;
+    }
+    if (!(fabs(r_hi - rint(r_hi)) > guard)) {
+      for (int it = 0; it < 4 && node_offset(nu_min, dnu, jhi + 1, nu0) <= cutoff; it++) jhi++;
+      for (int it = 0; it < 4 && node_offset(nu_min, dnu, jhi, nu0) > cutoff; it++) jhi--;
+    }
     long long jl = jlo < 0 ? 0 : (jlo > n_grid ? n_grid : jlo);
     long long jh = jhi < -1 ? -1 : (jhi > n_grid - 1 ? n_grid - 1 : jhi);
     if (jh >= jl) ev += (unsigned long long)(jh - jl + 1);
@@ -206,7 +217,14 @@ cudaError_t rox_launch_windows(const double* nu0, long long n_lines, const rox_g
                                int32_t* jlo, int32_t* jhi, int32_t* k0, float* f, float4* geo,
                                unsigned long long* evals, int32_t* unsorted, int32_t unsorted_value,
                                cudaStream_t s) {
-  k_windows<<<grid_for(n_lines), 256, 0, s>>>(nu0, n_lines, g->nu_min, g->dnu, 1.0 / g->dnu, g->n, cutoff, jlo, jhi, k0,
+  // rounding bound of the candidates and of the cutoff test, in index units: every quantity
+  // involved is at most |nu| + 2 cutoff in cm^-1 (or n + 8 in index units) for a line within
+  // reach; 16 double-precision ulps of each is a generous margin
+  const double inv_dnu = 1.0 / g->dnu;
+  const double nu_abs = fmax(fabs(g->nu_min), fabs(g->nu_min + (double)(g->n - 1) * g->dnu));
+  const double guard = 16.0 * 2.3e-16 * ((nu_abs + 2.0 * cutoff) * inv_dnu + (double)g->n + 8.0);
+  k_windows<<<grid_for(n_lines), 256, 0, s>>>(nu0, n_lines, g->nu_min, g->dnu, inv_dnu, guard, g->n, cutoff, jlo, jhi,
+                                               k0,
                                                f, geo, evals, unsorted, unsorted_value);
   return cudaGetLastError();
 }
