@@ -412,20 +412,76 @@ def run_gpu(args):
 
     # ---- end to end through the public API: pinned host -> device, sort, xsec, sigma -> host
     e2e_steps = 0 if args.no_e2e else args.steps
-    for _ in range(max(1, args.warmup // 2) if e2e_steps else 0):
-        upload_and_sort()
-        step()
-        sigma_host.copy_(sigma, non_blocking=True)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(e2e_steps):
-        upload_and_sort()
-        step()
-        sigma_host.copy_(sigma, non_blocking=True)
-    e1.record()
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
+    pipelined = e2e_steps > 0 and not (args.nodes or args.broadening or args.select is not None)
+    if pipelined:
+        # every step uploads and sorts its own list and reads its own sigma back; step k+1's upload
+        # and sort (copy stream) overlap step k's cross-section (main stream), the read-back runs on
+        # a third stream; a buffer is refilled once its previous cross-section is done and sigma is
+        # overwritten once its read-back is done
+        def twin(d):
+            return {k: (torch.empty_like(v) if isinstance(v, torch.Tensor) else v) for k, v in d.items()}
+        raw_b, lines_b = [raw, twin(raw)], [lines, twin(lines)]
+        sort_b = [sort_ws, torch.empty_like(sort_ws)]
+        sigma_b = [sigma, torch.empty_like(sigma)]
+        host_b = [sigma_host, torch.empty_like(sigma_host).pin_memory()]
+        main_s, copy_s, d2h_s = torch.cuda.current_stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        up_ev = [torch.cuda.Event() for _ in range(2)]
+        comp_ev = [torch.cuda.Event() for _ in range(2)]
+        d2h_ev = [torch.cuda.Event() for _ in range(2)]
+
+        def upload(b):
+            copy_s.wait_event(comp_ev[b])
+            with torch.cuda.stream(copy_s):
+                for k, v in pinned.items():
+                    raw_b[b][k].copy_(v, non_blocking=True)
+                rox.rox_sort_lines(raw_b[b], lines_b[b], None, sort_b[b], stream=copy_s)
+            up_ev[b].record(copy_s)
+
+        def compute(b):
+            main_s.wait_event(up_ev[b])
+            main_s.wait_event(d2h_ev[b])
+            rox.rox_xsec(lines_b[b], grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma_b[b], ws)
+            comp_ev[b].record(main_s)
+            d2h_s.wait_event(comp_ev[b])
+            with torch.cuda.stream(d2h_s):
+                host_b[b].copy_(sigma_b[b], non_blocking=True)
+            d2h_ev[b].record(d2h_s)
+
+        def e2e_run(k_steps):
+            upload(0)
+            for i in range(k_steps):
+                if i + 1 < k_steps:
+                    upload((i + 1) % 2)
+                compute(i % 2)
+            main_s.wait_event(d2h_ev[(k_steps - 1) % 2])
+
+        for b in range(2):
+            comp_ev[b].record(main_s)
+            d2h_ev[b].record(main_s)
+        e2e_run(max(2, args.warmup))
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main_s)
+        copy_s.wait_event(e0)
+        e2e_run(e2e_steps)
+        e1.record(main_s)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+    else:
+        for _ in range(max(1, args.warmup // 2) if e2e_steps else 0):
+            upload_and_sort()
+            step()
+            sigma_host.copy_(sigma, non_blocking=True)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(e2e_steps):
+            upload_and_sort()
+            step()
+            sigma_host.copy_(sigma, non_blocking=True)
+        e1.record()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
     if dist is not None:
         tt = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -494,8 +550,10 @@ def run_gpu(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
                         "d2h_bytes_per_step": sigma_bytes,
                         "ms_per_step": e2e_ms / e2e_steps if e2e_steps else None,
-                        "includes": "H2D of the unsorted list%s, rox_sort_lines, %s, D2H of sigma" % (
-                            " and the nodes" if args.nodes else "", "rox_xsec_nodes_batch" if args.nodes else "rox_xsec")},
+                        "includes": "H2D of the unsorted list%s, rox_sort_lines, %s, D2H of sigma%s" % (
+                            " and the nodes" if args.nodes else "", "rox_xsec_nodes_batch" if args.nodes else "rox_xsec",
+                            "; two list buffers, step k+1's upload and sort overlap step k's cross-section"
+                            if pipelined else "")},
                 "gpu_launches": args.steps * (6 if args.nodes or args.broadening else
                                               7 if args.select is not None else 5),
                 "gpu_launches_note": "per step: %swindows, strengths, strength scaling, %stile ranges, Voigt "
