@@ -169,11 +169,12 @@ __device__ __forceinline__ void edge_pair(const Rec& r0, const Rec& r1, int Aw, 
 // Pass 2 for a line whose slow zone meets the span: exactly the points pass 1 masked out
 // (t < t_z on the same rounded t, inside the window), with the full FP32 Faddeeva forms.
 // A zone of |z| < 6.5 takes the core forms at every point (rox_re_w_core holds 9e-6 out to
-// |z| = 7.1). Otherwise, per 32-point sub-span, one form for all points where possible: the
-// 3-level fraction if even the sub-span's point nearest the centre has |z| >= 10, the
-// 5-level one if |z| >= 6 there (both only get more accurate further out), else rox_re_w
-// per point. Accumulated into the warp's shared-memory row zacc[32 m + lane] (each lane
-// touches only its own points).
+// |z| = 7.1); on a uniform grid the lanes then take consecutive points of the zone rather than
+// aligned 32-point sub-spans (fewer, fuller warp steps). Otherwise, per 32-point sub-span, one
+// form for all points where possible: the 3-level fraction if even the sub-span's point nearest
+// the centre has |z| >= 10, the 5-level one if |z| >= 6 there (both only get more accurate
+// further out), else rox_re_w per point. Accumulated into the warp's shared-memory row zacc
+// (one add per line and point; within a warp step the lanes touch distinct points).
 template <bool NU>
 __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float Jf, float dnu_f, const float* daw,
                                           const float2* D, float* zacc) {
@@ -183,6 +184,19 @@ __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float
   const int lo = max(max(zlo, jlo), Aw), hi = min(min(zhi, jhi), Aw + ROX_SPAN - 1);
   if (lo > hi) return;
   const float invG = rq.d.x, y = rq.d.y, pcore = rq.d.z;
+  if (!NU && rq.d.w != 0.0f) {
+    // lanes on consecutive points of [lo, hi]; t rounded exactly as pass 1 rounds it
+    for (int k = lane; k <= hi - lo; k += 32) {
+      const int q = lo - Aw + k;
+      const float X0q = fmaf((float)(Aw + (q & 31)) - rq.a.x, dnu_f, -rq.a.y);
+      const float Xm = fmaf((float)(q & ~31), dnu_f, X0q);
+      const float t = fmaf(Xm, Xm, rq.a.z);
+      if (!(t < rq.b.w)) continue;
+      const float X = fmaf((float)(Aw + q) - rq.a.x, dnu_f, -rq.a.y);
+      zacc[q] += pcore * rox_re_w_core(daw, fabsf(X) * invG, y);
+    }
+    return;
+  }
   if (rq.d.w != 0.0f) {
     for (int m = (lo - Aw) >> 5; m <= ((hi - Aw) >> 5); m++) {
       const int j = Aw + 32 * m + lane;
