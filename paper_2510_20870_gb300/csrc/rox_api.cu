@@ -47,6 +47,11 @@ cudaError_t rox_launch_broad_T(const RoxBroadDev& B, const float* a_coef, long l
                                const double* temps, float* G, float* gN, cudaStream_t s);
 cudaError_t rox_launch_lorentz_out(const RoxBroadDev& B, const float* a_coef, long long n, double P_bar, double T,
                                    float* out, cudaStream_t s);
+size_t rox_compact_temp_bytes(long long n);
+cudaError_t rox_launch_compact(const float* S32_all, long long n, int n_temps, uint8_t* flags, int32_t* idx,
+                               long long* counts, void* temp, size_t temp_bytes, cudaStream_t s);
+cudaError_t rox_launch_tile_ranges_idx(const float4* geo, const int32_t* idx, const long long* count, long long n_max,
+                                       long long n_tiles, int32_t W, long long* lo, long long* hi, cudaStream_t s);
 cudaError_t rox_launch_keep_flags(const double* S_T, const int32_t* bin, const unsigned long long* binmax_bits,
                                   long long n, double rel, uint8_t* keep, cudaStream_t s);
 cudaError_t rox_launch_faddeeva(const float* x, const float* y, float* out, long long n, cudaStream_t s);
@@ -133,8 +138,15 @@ struct WsLayout {
   long long tail_cap;
   float2* node_d;      // user-provided nodes only: [n_tiles * ROX_SPAN] offsets, [n_tiles] bases
   float2* span_base;
-  int32_t* line_bin;   // main-contributor selection only: [n_lines] bins, [n_temps][n_bins] maxima
+  int32_t* line_bin;   // main-contributor selection only: [n_lines] bins, [n_temps][n_bins] maxima,
   unsigned long long* binmax;
+  uint8_t* keep_flags; //   per temperature the keep flags, the kept lines' indices and count, the span
+  int32_t* keep_idx;   //   ranges over those indices, and the compaction's scratch
+  long long* keep_count;
+  long long* keep_lo;
+  long long* keep_hi;
+  void* compact_tmp;
+  size_t compact_tmp_bytes;
   float* broad_G;      // broadening descriptions only: [n_temps][n_lines] broadeners' sums, [n_lines]
   float* broad_N;      //   natural widths
   size_t bytes;
@@ -172,11 +184,32 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, b
   }
   w.line_bin = nullptr;
   w.binmax = nullptr;
+  w.keep_flags = nullptr;
+  w.keep_idx = nullptr;
+  w.keep_count = nullptr;
+  w.keep_lo = nullptr;
+  w.keep_hi = nullptr;
+  w.compact_tmp = nullptr;
+  w.compact_tmp_bytes = 0;
   if (n_bins > 0) {
     w.line_bin = (int32_t*)(base + off);
     off += rox_align256((size_t)(n_lines > 0 ? n_lines : 1) * 4);
     w.binmax = (unsigned long long*)(base + off);
     off += rox_align256((size_t)n_temps * (size_t)n_bins * 8);
+    const size_t nl = (size_t)(n_lines > 0 ? n_lines : 1);
+    w.keep_flags = (uint8_t*)(base + off);
+    off += rox_align256((size_t)n_temps * nl);
+    w.keep_idx = (int32_t*)(base + off);
+    off += rox_align256((size_t)n_temps * nl * 4);
+    w.keep_count = (long long*)(base + off);
+    off += rox_align256((size_t)n_temps * 8);
+    w.keep_lo = (long long*)(base + off);
+    off += rox_align256((size_t)n_temps * (size_t)nt * 8);
+    w.keep_hi = (long long*)(base + off);
+    off += rox_align256((size_t)n_temps * (size_t)nt * 8);
+    w.compact_tmp_bytes = rox_compact_temp_bytes(n_lines);
+    w.compact_tmp = base + off;
+    off += rox_align256(w.compact_tmp_bytes);
   }
   w.broad_G = nullptr;
   w.broad_N = nullptr;
@@ -464,6 +497,19 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
                                 sel->rel, w.line_bin, w.binmax, w.S32, s)
             : rox_launch_scale_strengths(w.S_T, nl, n_temps, w.hdr->smax_bits, w.S32, s);
     if ((rc = cuda_check(se, "strength scaling kernel"))) return rc;
+    if (sel) {
+      // per temperature the kept lines as an index into the sorted list, and span ranges over it
+      if ((rc = cuda_check(rox_launch_compact(w.S32, nl, n_temps, w.keep_flags, w.keep_idx, w.keep_count,
+                                              w.compact_tmp, w.compact_tmp_bytes, s),
+                           "selection compaction")))
+        return rc;
+      for (int t = 0; t < n_temps; t++)
+        if ((rc = cuda_check(rox_launch_tile_ranges_idx(w.geo, w.keep_idx + (size_t)t * nl, w.keep_count + t, nl, nt,
+                                                        ROX_TILE, w.keep_lo + (size_t)t * nt,
+                                                        w.keep_hi + (size_t)t * nt, s),
+                             "selection span ranges")))
+          return rc;
+    }
     if (br && (rc = cuda_check(rox_launch_broad_T(bdev, lines->s_or_a, nl, n_temps, temps.data(), w.broad_G,
                                                   bdev.natural ? w.broad_N : nullptr, s),
                                "broadening kernel")))
@@ -487,6 +533,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   L0.dnu_f = on_nodes ? 0.0f : (float)grid->dnu;
   L0.nu_min_f = on_nodes ? 0.0f : (float)grid->nu_min;
   L0.width_f16 = lines->width_dtype == ROX_WIDTH_F16;
+  L0.idx = nullptr;
   L0.pad = 0;
   std::vector<RoxJobDev> jobs(n_pt);
   for (int k = 0; k < n_pt; k++) {
@@ -507,7 +554,30 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
     J.flags = flags;
     J.t_row = tidx[k];
   }
-  const int extras = (sel ? ROX_VX_SELECT : 0) | (br ? ROX_VX_BROAD : 0);
+  if (sel && nl > 0) {
+    // one list per temperature (its kept lines), launches of up to ROX_MAX_LISTS temperatures
+    for (int g0 = 0; g0 < n_temps; g0 += ROX_MAX_LISTS) {
+      const int ng = (n_temps - g0) < ROX_MAX_LISTS ? (n_temps - g0) : ROX_MAX_LISTS;
+      RoxListDev Ls[ROX_MAX_LISTS];
+      for (int l = 0; l < ng; l++) {
+        Ls[l] = L0;
+        Ls[l].idx = w.keep_idx + (size_t)(g0 + l) * nl;
+        Ls[l].span_lo = w.keep_lo + (size_t)(g0 + l) * nt;
+        Ls[l].span_hi = w.keep_hi + (size_t)(g0 + l) * nt;
+      }
+      std::vector<RoxJobDev> jg;
+      for (int k = 0; k < n_pt; k++)
+        if (tidx[k] >= g0 && tidx[k] < g0 + ng) {
+          jg.push_back(jobs[k]);
+          jg.back().list = tidx[k] - g0;
+        }
+      if ((rc = launch_voigt_jobs(Ls, ng, jg.data(), (int)jg.size(), w.hdr, w.tail_part, w.tail_cnt, w.tail_cap,
+                                  nblocks, s, false, ROX_VX_INDEX)))
+        return rc;
+    }
+    return ok();
+  }
+  const int extras = br ? ROX_VX_BROAD : 0;
   if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, w.tail_part, w.tail_cnt, w.tail_cap, nblocks, s,
                               on_nodes, extras)))
     return rc;
@@ -826,6 +896,7 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     L[l].gLT = nullptr;
     L[l].gLT_stride = 0;
     L[l].gN = nullptr;
+    L[l].idx = nullptr;
     L[l].node_d = nullptr;
     L[l].span_base = nullptr;
     L[l].n_lattice = P.lattice.n;

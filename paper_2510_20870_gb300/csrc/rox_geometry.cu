@@ -4,6 +4,8 @@
 // a hard wing cutoff, the lines that reach a wavenumber tile form one contiguous range,
 // found here without atomics from the sorted order.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_select.cuh>
+#include <thrust/iterator/counting_iterator.h>
 #include <cuda_fp16.h>
 #include "rox_internal.cuh"
 
@@ -163,6 +165,38 @@ __global__ void k_tile_ranges(const int32_t* __restrict__ jlo, const int32_t* __
 }
 
 // same, reading the window bounds out of the packed geometry records
+// k_tile_ranges_geo for a list given as indices into the sorted list (the kept lines of a
+// selection, still in nu0 order): line i of the list is geo[idx[i]], and the list length is
+// read on the device (*count, at most n_max).
+__global__ void k_tile_ranges_idx(const float4* __restrict__ geo, const int32_t* __restrict__ idx,
+                                  const long long* __restrict__ count, long long n_max, long long n_tiles, int32_t W,
+                                  long long* lo_out, long long* hi_out) {
+  const long long n_lines = *count;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= n_lines && i <= n_max; i += stride) {
+    long long ch_prev = 0, cl_prev = 0, ch = n_tiles, cl = n_tiles;
+    if (i > 0) {
+      float4 g = geo[idx[i - 1]];
+      ch_prev = tiles_reached_hi(__float_as_int(g.w), W, n_tiles);
+      cl_prev = tiles_passed_lo(__float_as_int(g.z), W, n_tiles);
+    }
+    if (i < n_lines) {
+      float4 g = geo[idx[i]];
+      ch = tiles_reached_hi(__float_as_int(g.w), W, n_tiles);
+      cl = tiles_passed_lo(__float_as_int(g.z), W, n_tiles);
+    }
+    for (long long t = ch_prev; t < ch; t++) lo_out[t] = i;
+    for (long long t = cl_prev; t < cl; t++) hi_out[t] = i;
+  }
+}
+
+// keep flag of every line and temperature: a selection marks dropped strengths with -0.0
+__global__ void k_kept_flags(const float* __restrict__ S32, long long total, uint8_t* flags) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride)
+    flags[i] = __float_as_uint(S32[i]) != 0x80000000u;
+}
+
 __global__ void k_tile_ranges_geo(const float4* __restrict__ geo, long long n_lines, long long n_tiles,
                                   int32_t W, long long* lo_out, long long* hi_out) {
   long long stride = (long long)gridDim.x * blockDim.x;
@@ -253,6 +287,33 @@ cudaError_t rox_launch_tile_ranges(const int32_t* jlo, const int32_t* jhi, long 
 cudaError_t rox_launch_tile_ranges_geo(const float4* geo, long long n_lines, long long n_tiles, int32_t W,
                                        long long* lo, long long* hi, cudaStream_t s) {
   k_tile_ranges_geo<<<grid_for(n_lines + 1), 256, 0, s>>>(geo, n_lines, n_tiles, W, lo, hi);
+  return cudaGetLastError();
+}
+
+// indices of the flagged lines, in order (CUB DeviceSelect::Flagged over 0..n-1), and their count
+size_t rox_compact_temp_bytes(long long n) {
+  size_t tb = 0;
+  cub::DeviceSelect::Flagged(nullptr, tb, thrust::counting_iterator<int32_t>(0), (const uint8_t*)nullptr,
+                             (int32_t*)nullptr, (long long*)nullptr, (int64_t)(n > 0 ? n : 1));
+  return tb;
+}
+
+cudaError_t rox_launch_compact(const float* S32_all, long long n, int n_temps, uint8_t* flags, int32_t* idx,
+                               long long* counts, void* temp, size_t temp_bytes, cudaStream_t s) {
+  const long long total = (long long)n_temps * n;
+  k_kept_flags<<<grid_for(total), 256, 0, s>>>(S32_all, total, flags);
+  cudaError_t e = cudaGetLastError();
+  for (int t = 0; t < n_temps && e == cudaSuccess; t++) {
+    size_t tb = temp_bytes;
+    e = cub::DeviceSelect::Flagged(temp, tb, thrust::counting_iterator<int32_t>(0), flags + (size_t)t * n,
+                                   idx + (size_t)t * n, counts + t, (int64_t)n, s);
+  }
+  return e;
+}
+
+cudaError_t rox_launch_tile_ranges_idx(const float4* geo, const int32_t* idx, const long long* count, long long n_max,
+                                       long long n_tiles, int32_t W, long long* lo, long long* hi, cudaStream_t s) {
+  k_tile_ranges_idx<<<grid_for(n_max + 1), 256, 0, s>>>(geo, idx, count, n_max, n_tiles, W, lo, hi);
   return cudaGetLastError();
 }
 

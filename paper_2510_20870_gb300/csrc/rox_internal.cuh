@@ -60,6 +60,9 @@ struct RoxListDev {
   const float* gLT;
   long long gLT_stride;
   const float* gN;
+  // indexed lists only (else NULL): the list's lines as indices into the sorted line arrays, in
+  // order (span ranges then count positions in this index)
+  const int32_t* idx;
   // user-provided nodes only (NULL on a uniform grid): per node its offset from the first node
   // of its span, per span that first node, both as double-float pairs {hi, lo}; geo then holds
   // {nu0 hi, nu0 lo, jlo, jhi}
@@ -88,7 +91,7 @@ struct RoxBroadDev {
 };
 
 // extras of a Voigt launch (kernel instantiations)
-#define ROX_VX_SELECT 1   // strengths carry a main-contributor selection
+#define ROX_VX_INDEX 1    // lists are subsets of the sorted lines given by an index (RoxListDev::idx)
 #define ROX_VX_BROAD 2    // widths from the broadening pass (RoxListDev::gLT, gN)
 
 struct RoxJobDev {

@@ -238,14 +238,14 @@ __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float
 }
 
 // NU: the lists are on user-provided nodes (node offsets in dynamic shared memory, one
-// ROX_SPAN row of float2 per warp). X: ROX_VX_SELECT (strengths carry a main-contributor
-// selection: zero-strength lines leave every pass, -0.0 ones leave the evaluation count) and
-// ROX_VX_BROAD (widths from the broadening pass). Each extra is compiled only into the
-// instantiations that use it: in this kernel even a few added instructions per line batch
-// cost several percent of the plain launch.
+// ROX_SPAN row of float2 per warp). X: ROX_VX_INDEX (each list is a subset of the sorted lines,
+// given by RoxListDev::idx, e.g. the kept lines of a main-contributor selection; span ranges
+// then count positions in that index) and ROX_VX_BROAD (widths from the broadening pass). Each
+// extra is compiled only into the instantiations that use it: in this kernel even a few added
+// instructions per line batch cost several percent of the plain launch.
 template <bool NU, int X>
 __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant__ RoxVoigtArgs A) {
-  constexpr bool SEL = (X & ROX_VX_SELECT) != 0;
+  constexpr bool IDX = (X & ROX_VX_INDEX) != 0;
   constexpr bool BRD = (X & ROX_VX_BROAD) != 0;
   extern __shared__ float2 s_nodes[];
   __shared__ float4 s_geo[ROX_WARPS][2][32];
@@ -328,13 +328,17 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
 #pragma unroll
       for (int m = 0; m < ROX_K; m++) { acc[m] = 0.f; tot[m] = 0.f; cmp[m] = 0.f; zacc[32 * m + lane] = 0.f; }
 
-      // stage batch 0; widths go through registers one batch ahead
+      // stage batch 0; widths go through registers one batch ahead (with an index, the
+      // positions' line numbers two batches ahead)
       float gref = 0.f, nt = 0.f;
+      long long li_n = 0;   // IDX: line number of this lane's position in the next batch
       if (plo + lane < phi) {
-        cp_async16(&geo_st[0][lane], &Lst.geo[plo + lane]);
-        cp_async4(&S_st[0][lane], &S_row[plo + lane]);
-        load_widths<BRD>(J, Lst, f16, plo + lane, gref, nt);
+        const long long li = IDX ? (long long)Lst.idx[plo + lane] : plo + lane;
+        cp_async16(&geo_st[0][lane], &Lst.geo[li]);
+        cp_async4(&S_st[0][lane], &S_row[li]);
+        load_widths<BRD>(J, Lst, f16, li, gref, nt);
       }
+      if (IDX && plo + 32 + lane < phi) li_n = Lst.idx[plo + 32 + lane];
       cp_async_commit();
       int nb = 0;
       for (long long b0 = plo; b0 < phi; b0 += 32, nb++) {
@@ -342,16 +346,17 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         const int buf = nb & 1;
         float gref_n = 0.f, nt_n = 0.f;
         if (b0 + 32 + lane < phi) {
-          cp_async16(&geo_st[buf ^ 1][lane], &Lst.geo[b0 + 32 + lane]);
-          cp_async4(&S_st[buf ^ 1][lane], &S_row[b0 + 32 + lane]);
-          load_widths<BRD>(J, Lst, f16, b0 + 32 + lane, gref_n, nt_n);
+          const long long li = IDX ? li_n : b0 + 32 + lane;
+          cp_async16(&geo_st[buf ^ 1][lane], &Lst.geo[li]);
+          cp_async4(&S_st[buf ^ 1][lane], &S_row[li]);
+          load_widths<BRD>(J, Lst, f16, li, gref_n, nt_n);
         }
+        if (IDX && b0 + 64 + lane < phi) li_n = Lst.idx[b0 + 64 + lane];
         cp_async_commit();
         cp_async_wait1();   // this lane's copies of the current batch have landed
 
         // ---- per-line constants (lane <-> line b0 + lane)
         Rec r;
-        bool has_S = false;   // zero strength (below FP32, or -0.0: dropped by a selection): nothing to add
         if (lane < cnt) {
           const float4 g = geo_st[buf][lane];
           const float Sp = S_st[buf][lane];
@@ -371,13 +376,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
           const float gG = nu0f * J.gG_fac;
           const float gL = BRD ? fmaf(gref, J.p_fac, nt) : gref * exp2f(nt * J.l2_ratio) * J.p_fac;
           const long long ov = min((long long)jhi, whi) - max((long long)jlo, wlo) + 1;
-          if constexpr (SEL) {
-            has_S = Sp != 0.0f;
-            const bool dropped = __float_as_uint(Sp) == 0x80000000u;   // -0.0: not kept by the selection
-            if (ov > 0 && !dropped) evals += (unsigned long long)ov;
-          } else {
-            if (ov > 0) evals += (unsigned long long)ov;
-          }
+          if (ov > 0) evals += (unsigned long long)ov;
           const float gG2 = gG * gG, gL2 = gL * gL;
           const float pY = Sp * gL * ROX_INV_PI;
           const float invG = 1.0f / gG;
@@ -426,7 +425,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         // unmasked pairs; covering lines with a slow zone in masked pairs; window-edge lines in
         // pairs with window masks. The orders are fixed, so the sum is reproducible.
         const unsigned cls = __float_as_uint(r.b.z);
-        const bool live = SEL ? (lane < cnt && has_S) : lane < cnt;
+        const bool live = lane < cnt;
         unsigned cmask = __ballot_sync(0xffffffffu, live && cls == 1u);
         unsigned zmask = __ballot_sync(0xffffffffu, live && cls == 3u);
         const unsigned emask = __ballot_sync(0xffffffffu, live && !(cls & 1u));
@@ -589,12 +588,12 @@ cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, in
     k_voigt<true, 0><<<n_blocks, ROX_THREADS, ROX_NODES_SMEM, s>>>(A);
   } else if (extras == 0) {
     k_voigt<false, 0><<<n_blocks, ROX_THREADS, 0, s>>>(A);
-  } else if (extras == ROX_VX_SELECT) {
-    k_voigt<false, ROX_VX_SELECT><<<n_blocks, ROX_THREADS, 0, s>>>(A);
+  } else if (extras == ROX_VX_INDEX) {
+    k_voigt<false, ROX_VX_INDEX><<<n_blocks, ROX_THREADS, 0, s>>>(A);
   } else if (extras == ROX_VX_BROAD) {
     k_voigt<false, ROX_VX_BROAD><<<n_blocks, ROX_THREADS, 0, s>>>(A);
   } else {
-    return cudaErrorNotSupported;   // no entry point combines a selection with broadening
+    return cudaErrorNotSupported;   // no entry point combines an indexed list with broadening
   }
   return cudaGetLastError();
 }

@@ -86,9 +86,9 @@ def test_selected_cross_sections():
 
 
 def test_rel_zero_equals_unselected():
-    """rel = 0 keeps every line that reaches the grid: the unselected result. Not bit for bit:
-    the selection kernel also leaves out lines whose strength underflows FP32 (exact zeros),
-    which changes how the other lines are paired and so the last bits."""
+    """rel = 0 keeps every line that reaches the grid: the unselected result (the kept-line
+    index then lists every line the spans reach, in the same order, so the sums agree to the
+    last bit in practice; the check allows rounding)."""
     w = rs.CONFIGS[1]
     L = oracle.sort_lines(rs.make_lines(w))
     grid = rs.grid_of(w)
