@@ -120,3 +120,24 @@ def test_selection_full_size_sample():
         check_sigma(got[0][j0:j0 + 96], ref, M=M, label="selected full size window %d" % j0)
     assert evals == oracle.count_evals(Lk["nu0"], *grid, w.cutoff)
     print("SELECTION config 2: kept %d of %d lines, %d evaluations" % (keep.sum(), keep.size, evals))
+
+
+def test_selection_more_temperatures_than_one_launch():
+    """Ten distinct temperatures: one kept-line list each, grouped eight per launch."""
+    w = rs.CONFIGS[1]
+    L = oracle.sort_lines(rs.make_lines(w, 0, 4000))
+    grid = (2000.0, 0.02, 25001)
+    dl = to_device(L, torch)
+    temps = np.linspace(300.0, 3000.0, 10)
+    pts = []
+    for k, T in enumerate(temps):
+        Qt, Qr = q_pair(w, T)
+        pts.append((10.0 ** (k / 3.0 - 2.0), float(T), Qt))
+    got, evals = _select_xsec(dl, grid, pts, Qr, w.mass_amu, 25.0, 1e-4, 2.0)
+    total = 0
+    for k, (P, T, Qt) in enumerate(pts):
+        Lk, keep = oracle.select_lines(L, grid, 25.0, T, Qt, Qr, 1e-4, 2.0)
+        ref = oracle.xsec_windowed(Lk, grid, P, T, Qt, Qr, w.mass_amu, 25.0)
+        check_sigma(got[k], ref, label="selected, 10 temperatures, T=%g" % T)
+        total += oracle.count_evals(Lk["nu0"], *grid, 25.0)
+    assert evals == total
