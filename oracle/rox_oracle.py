@@ -47,6 +47,10 @@ Readings where the paper is silent (all listed in the design doc as well):
       (J beyond the table takes its last entry); the natural term (Lorentz HWHM of the
       Einstein-A decay, c in cm/s) only for ExoMol lists, where s_or_a is A. Lorentz widths
       add, as Lorentzians convolve into one.
+  R17 CIA restructuring ("Combine and save": CIA coefficients restructured into a wavelength- and
+      temperature-dependent grid): per output temperature, the first input block of that
+      temperature covering a node, linear interpolation in wavenumber between its bracketing
+      samples (float64, one written order), 0 where no block covers the node (cia_regrid).
 """
 import numpy as np
 from scipy.special import wofz
@@ -57,7 +61,7 @@ __all__ = [
     "voigt_profile", "grid_nodes", "window_indices", "count_evals",
     "xsec_bruteforce", "xsec_windowed", "xsec_points", "xsec_window", "sort_lines",
     "fixed_resolution_nodes", "node_windows", "xsec_nodes", "xsec_nodes_bruteforce",
-    "select_bins", "select_mask", "select_lines", "apply_broadening", "lorentz_width_broadened",
+    "select_bins", "select_mask", "select_lines", "apply_broadening", "lorentz_width_broadened", "cia_regrid",
 ]
 
 # R1: CODATA 2018 exact SI values where defined
@@ -395,3 +399,39 @@ def select_lines(lines_sorted, grid, cutoff, T, Q_T, Q_ref, rel, bin_width):
     origin, n_bins = select_bins(grid, cutoff, bin_width)
     keep = select_mask(lines_sorted["nu0"], S, rel, bin_width, origin, n_bins)
     return {k: (v[keep] if isinstance(v, np.ndarray) else v) for k, v in lines_sorted.items()}, keep
+
+
+# ---------------------------------------------------------------- R17: CIA restructuring
+def cia_regrid(T_block, nu_blocks, k_blocks, T_out, nu_grid):
+    """R17 (section "Functionality", "Combine and save": CIA coefficients read from the input
+    files are restructured into a wavelength- and temperature-dependent grid). Blocks b hold a
+    temperature T_block[b] and strictly increasing wavenumbers nu_blocks[b] with coefficients
+    k_blocks[b]. Row t of the result on nodes nu_grid: at each node, the first block (input
+    order) with T_block == T_out[t] whose range [nu_first, nu_last] contains the node, linearly
+    interpolated between its bracketing samples as
+        k_i + (k_{i+1} - k_i) * ((nu - nu_i) / (nu_{i+1} - nu_i))   (float64, in that order),
+    the sample's own value at a sample, and 0 where no such block covers the node."""
+    nu_grid = np.asarray(nu_grid, dtype=np.float64)
+    out = np.zeros((len(T_out), nu_grid.size), dtype=np.float64)
+    for t, Tt in enumerate(T_out):
+        done = np.zeros(nu_grid.size, dtype=bool)
+        for b, Tb in enumerate(T_block):
+            if Tb != Tt:
+                continue
+            x = np.asarray(nu_blocks[b], dtype=np.float64)
+            y = np.asarray(k_blocks[b], dtype=np.float64)
+            inside = (~done) & (nu_grid >= x[0]) & (nu_grid <= x[-1])
+            v = nu_grid[inside]
+            i = np.searchsorted(x, v, side="right") - 1          # x[i] <= v < x[i+1], or v == x[-1]
+            i = np.minimum(i, x.size - 2) if x.size > 1 else np.zeros_like(i)
+            if x.size == 1:
+                val = np.full(v.size, y[0])
+            else:
+                val = y[i] + (y[i + 1] - y[i]) * ((v - x[i]) / (x[i + 1] - x[i]))
+                at = v == x[i]
+                val[at] = y[i][at]
+                last = v == x[-1]
+                val[last] = y[-1]
+            out[t, inside] = val
+            done |= inside
+    return out

@@ -371,6 +371,56 @@ def pin_broadening_table_and_natural(o):
                        1000.0), nat, rtol=1e-9, atol=1e-300)
 
 
+# ---------------------------------------------------------------- CIA restructuring (R17)
+def _cia_brute(T_block, nu_blocks, k_blocks, T_out, grid_nu):
+    out = []
+    for Tt in T_out:
+        row = []
+        for v in grid_nu:
+            val = 0.0
+            for Tb, x, y in zip(T_block, nu_blocks, k_blocks):
+                if Tb != Tt or not (x[0] <= v <= x[-1]):
+                    continue
+                if len(x) == 1 or v == x[-1]:
+                    val = float(y[-1])
+                else:
+                    i = 0
+                    while not (x[i] <= v < x[i + 1]):
+                        i += 1
+                    val = float(y[i]) if v == x[i] else float(y[i] + (y[i + 1] - y[i]) * ((v - x[i]) / (x[i + 1] - x[i])))
+                break
+            row.append(val)
+        out.append(row)
+    return np.array(out)
+
+
+def pin_cia_regrid(o):
+    rng = np.random.default_rng(17)
+    xa = np.sort(rng.uniform(10.0, 500.0, 40)); ya = rng.uniform(1e-46, 1e-44, 40)
+    xb = np.sort(rng.uniform(300.0, 900.0, 30)); yb = rng.uniform(1e-46, 1e-44, 30)
+    xc = np.array([100.0, 250.0]); yc = np.array([3e-45, 5e-45])
+    Tb = [300.0, 300.0, 1000.0]
+    grid = np.concatenate([np.linspace(0.0, 1000.0, 701), xa[[0, 5, -1]], xb[[0, -1]], [250.0]])
+    grid = np.unique(grid)
+    got = o.cia_regrid(Tb, [xa, xb, xc], [ya, yb, yc], [300.0, 1000.0, 2000.0], grid)
+    assert np.array_equal(got, _cia_brute(Tb, [xa, xb, xc], [ya, yb, yc], [300.0, 1000.0, 2000.0], grid))
+    # samples exactly, coverage inclusive, first block wins where two overlap, zero elsewhere
+    for x, y in ((xa, ya),):
+        for q in (0, 5, -1):
+            assert got[0, np.searchsorted(grid, x[q])] == y[q]
+    assert got[0, np.searchsorted(grid, xb[-1])] == yb[-1]
+    ov = (grid > xb[0]) & (grid < xa[-1])
+    ref_a = o.cia_regrid([300.0], [xa], [ya], [300.0], grid[ov])[0]
+    assert ov.any() and np.array_equal(got[0, ov], ref_a)
+    assert np.all(got[0, grid < xa[0]] == 0.0) and np.all(got[0, grid > xb[-1]] == 0.0)
+    assert np.all(got[2] == 0.0)                       # a temperature without blocks
+    # linear coefficients are reproduced (closed form)
+    xl = np.sort(rng.uniform(50.0, 950.0, 25)); yl = 2e-46 + 3e-48 * xl
+    v = np.linspace(xl[0], xl[-1], 333)
+    lin = o.cia_regrid([500.0], [xl], [yl], [500.0], v)[0]
+    assert np.allclose(lin, 2e-46 + 3e-48 * v, rtol=1e-13, atol=0)
+
+
 PINS = [pin_c2, pin_hitran_at_tref, pin_exomol_from_oscillator_strength, pin_hitran_exomol_consistency,
         pin_partition_table, pin_doppler_published, pin_lorentz_closed_forms, pin_voigt_gaussian_limit,
         pin_voigt_centre_erfcx, pin_voigt_lorentz_limit, pin_voigt_convolution_quadrature,
@@ -378,7 +428,7 @@ PINS = [pin_c2, pin_hitran_at_tref, pin_exomol_from_oscillator_strength, pin_hit
         pin_linearity_and_permutation, pin_grid_shift, pin_cutoff_inclusive, pin_count_evals_bruteforce,
         pin_points_equal_full, pin_nodes_uniform_equals_windowed, pin_nodes_bruteforce, pin_node_windows,
         pin_fixed_resolution, pin_select_rules, pin_select_sum, pin_broadening_single_equals_power_law,
-        pin_broadening_mixture, pin_broadening_table_and_natural]
+        pin_broadening_mixture, pin_broadening_table_and_natural, pin_cia_regrid]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -484,3 +534,23 @@ def test_mutation_natural_width_fwhm(monkeypatch):
         return g
     monkeypatch.setattr(orc, "lorentz_width_broadened", wrong)
     assert _fails(pin_broadening_table_and_natural)
+
+
+def test_mutation_cia_last_block_wins(monkeypatch):
+    real = orc.cia_regrid
+    monkeypatch.setattr(orc, "cia_regrid", lambda Tb, xs, ys, To, g: real(Tb[::-1], xs[::-1], ys[::-1], To, g))
+    assert _fails(pin_cia_regrid)
+
+
+def test_mutation_cia_step_instead_of_linear(monkeypatch):
+    def wrong(Tb, xs, ys, To, g):   # the lower sample's value instead of the interpolation
+        g = np.asarray(g, dtype=np.float64)
+        out = np.zeros((len(To), g.size))
+        for t, Tt in enumerate(To):
+            for T, x, y in zip(Tb, xs, ys):
+                if T == Tt:
+                    m = (g >= x[0]) & (g <= x[-1]) & (out[t] == 0)
+                    out[t, m] = np.asarray(y)[np.searchsorted(x, g[m], side="right") - 1]
+        return out
+    monkeypatch.setattr(orc, "cia_regrid", wrong)
+    assert _fails(pin_cia_regrid)
