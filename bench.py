@@ -58,6 +58,9 @@ def parse():
                     help="main-contributor selection: keep lines with S >= REL x the largest S of their nu0 bin "
                          "(rox_xsec_select_batch)")
     ap.add_argument("--select-bin", type=float, default=1.0, help="selection bin width (cm^-1)")
+    ap.add_argument("--cia", action="store_true",
+                    help="CIA restructuring: 40 synthetic temperatures of coefficient blocks onto config 2's grid "
+                         "(rox_cia_regrid); prints its own JSON line")
     ap.add_argument("--broadening", action="store_true",
                     help="broadener mixture and natural broadening (rox_xsec_broadened_batch): 0.85 H2 from per-line "
                          "columns + 0.15 He from a J table, plus A/(4 pi c)")
@@ -683,10 +686,52 @@ def run_stream_config(args):
                       "clocks": clocks.summary()}))
 
 
+def run_cia(args):
+    """CIA restructuring: synthetic coefficient blocks of 40 temperatures (1-3 blocks each, 4000
+    samples per temperature over 20-10000 cm^-1) onto config 2's grid, 2,970,001 points per row."""
+    import torch
+    import paper_2510_20870_gb300 as rox
+    grid = rs.grid_of(rs.CONFIGS[2])
+    temps = list(np.linspace(200.0, 3000.0, 40))
+    Tb, off, nu_h, k_h = rs.cia_blocks(60, temps, samples=4000)
+    nu, k = torch.from_numpy(nu_h).cuda(), torch.from_numpy(k_h).cuda()
+    out = torch.empty((len(temps), grid[2]), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        rox.rox_cia_regrid(Tb, off, nu, k, grid, temps, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record()
+        for _ in range(args.steps):
+            rox.rox_cia_regrid(Tb, off, nu, k, grid, temps, out)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    points = len(temps) * grid[2]
+    out_bytes = points * 8
+    peak = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) else 6800.0
+    achieved = out_bytes / (ms * 1e-3) / 1e9
+    print(json.dumps({"metric": "CIA grid points/s", "value": points / (ms * 1e-3), "unit": "points/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "CIA restructuring: %d temperatures (%d blocks, %d samples) onto %d "
+                                             "points (300-30000 cm^-1 at 0.01)" % (len(temps), len(Tb), nu_h.size,
+                                                                                   grid[2]),
+                                 "l2": "output %.0f MB per step, larger than L2" % (out_bytes / 1e6)},
+                      "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                   "frac": achieved / peak, "traffic": None,
+                                   "note": "algorithmic bytes: the float64 output written once (inputs %.1f MB, "
+                                           "L2-resident)" % ((nu_h.size * 16) / 1e6)},
+                      "gpu_launches": args.steps, "clocks": clocks.summary()}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.cia:
+        run_cia(args)
     elif args.config == 3:
         run_batch_config(args)
     elif args.config == 4:

@@ -287,6 +287,35 @@ int rox_xsec_nodes_batch(const rox_lines* lines, const rox_nodes* nodes, int n_p
 int rox_node_windows(const double* nu0_sorted, int64_t n_lines, const rox_nodes* nodes,
                      double cutoff, int32_t* jlo, int32_t* jhi, void* stream);
 
+/* CIA restructuring (paper, "Functionality of pyROX", "Combine and save": for CIA calculations
+ * the coefficients read from the input files are restructured into a wavelength- and
+ * temperature-dependent grid). Input: n_blocks blocks (1..ROX_CIA_MAX_BLOCKS), block b at
+ * temperature T_block[b] (HOST) with samples offset[b] .. offset[b+1]-1 (offset HOST, [n_blocks+1],
+ * offset[0] = 0, at least one sample per block) of the DEVICE arrays nu (cm^-1, strictly
+ * increasing within a block; not checked) and k (coefficients, any unit). Output: out
+ * [n_T][n] double (DEVICE), row t for temperature T_out[t] (HOST, n_T <= ROX_CIA_MAX_TEMPS) on the
+ * grid's points (nu_min + j dnu, one multiply and one add, or the given nodes): at each point
+ * the first block (input order) with T_block == T_out[t] whose sample range contains it, linearly
+ * interpolated between its bracketing samples, k_i + (k_{i+1} - k_i) (nu - nu_i) / (nu_{i+1} - nu_i),
+ * in double precision (within a few ulps of that expression; a sample's own value at a sample),
+ * and 0 where no such block covers the point. Nodes may come in any order (ascending is the
+ * fast case: each lane walks its intervals forward). Returns ROX_EINVAL, writing nothing, for a
+ * bad block layout or count; launch errors as for the other entry points. */
+#define ROX_CIA_MAX_BLOCKS 256
+#define ROX_CIA_MAX_TEMPS 4096
+typedef struct rox_cia {
+  int32_t n_blocks;
+  int32_t pad;
+  const double* T_block;
+  const int64_t* offset;
+  const double* nu;
+  const double* k;
+} rox_cia;
+int rox_cia_regrid(const rox_cia* cia, const rox_grid* grid, int n_T, const double* T_out,
+                   double* out, void* stream);
+int rox_cia_regrid_nodes(const rox_cia* cia, const rox_nodes* nodes, int n_T, const double* T_out,
+                         double* out, void* stream);
+
 /* Synchronises `stream` and returns the device-side status recorded in `ws` by the last
  * rox_xsec / rox_xsec_batch / rox_xsec_nodes_batch call that used it: ROX_OK, ROX_EUNSORTED
  * (lines not in ascending nu0: no sigma was written), ROX_EGRID (bad nodes: no sigma was

@@ -61,6 +61,11 @@ class RoxBroadening(ctypes.Structure):
                 ("table_len", ctypes.c_int64)]
 
 
+class RoxCia(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int32), ("pad", ctypes.c_int32), ("T_block", ctypes.c_void_p),
+                ("offset", ctypes.c_void_p), ("nu", ctypes.c_void_p), ("k", ctypes.c_void_p)]
+
+
 class RoxPrepared(ctypes.Structure):
     _fields_ = [("lines", RoxLines), ("lattice", RoxGrid), ("cutoff", ctypes.c_double), ("state", ctypes.c_void_p),
                 ("span_lo", ctypes.c_void_p), ("span_hi", ctypes.c_void_p), ("n_spans", ctypes.c_int64)]
@@ -107,6 +112,8 @@ def _load():
                                                  P]),
         "rox_line_select": (ctypes.c_int, [P, P, D, D, D, D, P, P, P, ctypes.c_size_t, P]),
         "rox_lorentz_widths": (ctypes.c_int, [P, P, D, D, P, P]),
+        "rox_cia_regrid": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P]),
+        "rox_cia_regrid_nodes": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P]),
         "rox_xsec_broadened_workspace_size": (ctypes.c_size_t, [I64, P, ctypes.c_int]),
         "rox_xsec_broadened_batch": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P,
                                                     ctypes.c_size_t, P]),
@@ -319,6 +326,25 @@ def rox_xsec_broadened_batch(lines, grid, br, P_bar, T, Q_T, Q_ref, mass_amu, cu
     _check(lib.rox_xsec_broadened_batch(ctypes.byref(L), ctypes.byref(G), ctypes.byref(B), n_pt, arr(*P_bar), arr(*T),
                                         arr(*Q_T), Q_ref, mass_amu, cutoff, flags, _ptr(sigma_out), _ptr(ws),
                                         ws.numel(), _stream(stream)))
+
+
+def _cia_call(fn, grid_arg, T_block, offset, nu, k, T_out, out, stream):
+    nb = len(T_block)
+    tb = (ctypes.c_double * nb)(*[float(x) for x in T_block])
+    off = (ctypes.c_int64 * (nb + 1))(*[int(x) for x in offset])
+    to = (ctypes.c_double * len(T_out))(*[float(x) for x in T_out])
+    C = RoxCia(nb, 0, ctypes.cast(tb, ctypes.c_void_p), ctypes.cast(off, ctypes.c_void_p), _ptr(nu).value, _ptr(k).value)
+    _check(fn(ctypes.byref(C), ctypes.byref(grid_arg), len(T_out), to, _ptr(out), _stream(stream)))
+
+
+def rox_cia_regrid(T_block, offset, nu, k, grid, T_out, out, stream=None):
+    """CIA blocks (temperatures and offsets on the host; nu, k float64 CUDA tensors, blocks
+    concatenated) onto the uniform grid: out [len(T_out)][n] float64."""
+    _cia_call(lib.rox_cia_regrid, grid_struct(grid), T_block, offset, nu, k, T_out, out, stream)
+
+
+def rox_cia_regrid_nodes(T_block, offset, nu, k, nodes, T_out, out, stream=None):
+    _cia_call(lib.rox_cia_regrid_nodes, nodes_struct(nodes), T_block, offset, nu, k, T_out, out, stream)
 
 
 def rox_xsec(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, stream=None):

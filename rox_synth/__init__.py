@@ -14,8 +14,8 @@ a line list too large for it.
 """
 from .philox import philox4x32_10, uniform01
 from .workloads import (CONFIGS, FIXED_R, SERVE_LISTS, Workload, fixed_resolution_grid, grid_of, irregular_nodes,
-                        make_lines, make_lines_at, nu0_in_chunks, pt_points, q_table, serve_requests, j_lower_of)
+                        make_lines, make_lines_at, nu0_in_chunks, pt_points, q_table, serve_requests, j_lower_of, cia_blocks)
 
 __all__ = ["philox4x32_10", "uniform01", "CONFIGS", "SERVE_LISTS", "Workload", "make_lines", "make_lines_at",
            "nu0_in_chunks", "q_table", "grid_of", "pt_points", "serve_requests", "FIXED_R", "fixed_resolution_grid",
-           "irregular_nodes", "j_lower_of"]
+           "irregular_nodes", "j_lower_of", "cia_blocks"]

@@ -234,3 +234,34 @@ def j_lower_of(w: Workload, start: int = 0, count: int = None):
     if count is None:
         count = w.n_lines - start
     return np.floor(100.0 * uniform01(w.seed, 41, start, count)).astype(np.int32)
+
+
+def cia_blocks(seed: int, temps, lo: float = 20.0, hi: float = 10000.0, samples: int = 4000):
+    """Synthetic CIA tables standing in for collision-induced-absorption files (no data files
+    are available offline): per temperature one to three blocks covering parts of [lo, hi] with
+    irregular, strictly increasing wavenumbers and smooth positive coefficients (cm^5
+    molecule^-2 scale). Returns (T_block list, offsets [n_blocks + 1], nu, k) with the blocks
+    concatenated (Philox stream 43 of `seed`)."""
+    T_block, offsets, nus, ks = [], [0], [], []
+    draw = 0
+    for T in temps:
+        u = uniform01(seed, 43, draw, 4)
+        draw += 4
+        nb = 1 + int(3 * u[0])
+        edges = np.linspace(lo, hi, nb + 1)
+        for b in range(nb):
+            a, c = edges[b], edges[b + 1]
+            m = max(2, samples // nb)
+            r = uniform01(seed, 43, draw, m)
+            draw += m
+            x = np.unique(a + (c - a) * np.sort(r))
+            x[0], x[-1] = a, c
+            x = np.unique(x)
+            centre = lo + (hi - lo) * u[1]
+            k = 1e-45 * (float(T) / 300.0) ** 0.5 * (np.exp(-((x - centre) / (0.1 * (hi - lo))) ** 2)
+                                                      + 0.3 * np.exp(-((x - lo) / (0.02 * (hi - lo))) ** 2) + 0.01)
+            T_block.append(float(T))
+            nus.append(x)
+            ks.append(k)
+            offsets.append(offsets[-1] + x.size)
+    return T_block, np.array(offsets, dtype=np.int64), np.concatenate(nus), np.concatenate(ks)
