@@ -299,8 +299,13 @@ int rox_node_windows(const double* nu0_sorted, int64_t n_lines, const rox_nodes*
  * interpolated between its bracketing samples, k_i + (k_{i+1} - k_i) (nu - nu_i) / (nu_{i+1} - nu_i),
  * in double precision (within a few ulps of that expression; a sample's own value at a sample),
  * and 0 where no such block covers the point. Nodes may come in any order (ascending is the
- * fast case: each lane walks its intervals forward). Returns ROX_EINVAL, writing nothing, for a
- * bad block layout or count; launch errors as for the other entry points. */
+ * fast case: each lane walks its intervals forward). On the uniform grid the points of each
+ * interval are those the definition assigns to it on the rounded grid values, the value steps
+ * from the interval's first point by the constant increment per grid point (within 32 roundings of
+ * the expression above, exact at samples); ws: DEVICE scratch of rox_cia_workspace_size(n_blocks,
+ * offset[n_blocks]) bytes, 8-byte aligned, not kept between calls. Returns ROX_EINVAL, writing
+ * nothing, for a bad block layout or count or a short workspace; launch errors as for the other
+ * entry points. */
 #define ROX_CIA_MAX_BLOCKS 256
 #define ROX_CIA_MAX_TEMPS 4096
 typedef struct rox_cia {
@@ -311,8 +316,9 @@ typedef struct rox_cia {
   const double* nu;
   const double* k;
 } rox_cia;
+size_t rox_cia_workspace_size(int32_t n_blocks, int64_t n_samples);
 int rox_cia_regrid(const rox_cia* cia, const rox_grid* grid, int n_T, const double* T_out,
-                   double* out, void* stream);
+                   double* out, void* ws, size_t ws_bytes, void* stream);
 int rox_cia_regrid_nodes(const rox_cia* cia, const rox_nodes* nodes, int n_T, const double* T_out,
                          double* out, void* stream);
 

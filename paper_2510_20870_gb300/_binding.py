@@ -112,7 +112,8 @@ def _load():
                                                  P]),
         "rox_line_select": (ctypes.c_int, [P, P, D, D, D, D, P, P, P, ctypes.c_size_t, P]),
         "rox_lorentz_widths": (ctypes.c_int, [P, P, D, D, P, P]),
-        "rox_cia_regrid": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P]),
+        "rox_cia_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int64]),
+        "rox_cia_regrid": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P, ctypes.c_size_t, P]),
         "rox_cia_regrid_nodes": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P]),
         "rox_xsec_broadened_workspace_size": (ctypes.c_size_t, [I64, P, ctypes.c_int]),
         "rox_xsec_broadened_batch": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P,
@@ -328,19 +329,28 @@ def rox_xsec_broadened_batch(lines, grid, br, P_bar, T, Q_T, Q_ref, mass_amu, cu
                                         ws.numel(), _stream(stream)))
 
 
-def _cia_call(fn, grid_arg, T_block, offset, nu, k, T_out, out, stream):
+def _cia_call(fn, grid_arg, T_block, offset, nu, k, T_out, out, stream, ws=None):
     nb = len(T_block)
     tb = (ctypes.c_double * nb)(*[float(x) for x in T_block])
     off = (ctypes.c_int64 * (nb + 1))(*[int(x) for x in offset])
     to = (ctypes.c_double * len(T_out))(*[float(x) for x in T_out])
     C = RoxCia(nb, 0, ctypes.cast(tb, ctypes.c_void_p), ctypes.cast(off, ctypes.c_void_p), _ptr(nu).value, _ptr(k).value)
-    _check(fn(ctypes.byref(C), ctypes.byref(grid_arg), len(T_out), to, _ptr(out), _stream(stream)))
+    if ws is None:
+        _check(fn(ctypes.byref(C), ctypes.byref(grid_arg), len(T_out), to, _ptr(out), _stream(stream)))
+    else:
+        _check(fn(ctypes.byref(C), ctypes.byref(grid_arg), len(T_out), to, _ptr(out), _ptr(ws), ws.numel(),
+                  _stream(stream)))
 
 
-def rox_cia_regrid(T_block, offset, nu, k, grid, T_out, out, stream=None):
+def rox_cia_workspace_size(n_blocks, n_samples):
+    return int(lib.rox_cia_workspace_size(int(n_blocks), int(n_samples)))
+
+
+def rox_cia_regrid(T_block, offset, nu, k, grid, T_out, out, ws, stream=None):
     """CIA blocks (temperatures and offsets on the host; nu, k float64 CUDA tensors, blocks
-    concatenated) onto the uniform grid: out [len(T_out)][n] float64."""
-    _cia_call(lib.rox_cia_regrid, grid_struct(grid), T_block, offset, nu, k, T_out, out, stream)
+    concatenated) onto the uniform grid: out [len(T_out)][n] float64; ws: uint8 CUDA tensor of
+    rox_cia_workspace_size(len(T_block), offset[-1]) bytes."""
+    _cia_call(lib.rox_cia_regrid, grid_struct(grid), T_block, offset, nu, k, T_out, out, stream, ws=ws)
 
 
 def rox_cia_regrid_nodes(T_block, offset, nu, k, nodes, T_out, out, stream=None):

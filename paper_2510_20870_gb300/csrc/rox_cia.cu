@@ -4,13 +4,28 @@
 // coefficients read from the input files are restructured into a wavelength- and
 // temperature-dependent grid.
 //
-// A warp takes a tile of 32 x ROX_CIA_RUN consecutive points of one row, lane l the points
-// p0 + l + 32 s (coalesced stores). For each block of the row's temperature, in input order,
-// a lane finds the bracketing interval of its first point by binary search and then walks it
-// forward (the points increase), interpolating with the interval's reciprocal width formed
-// once per interval; the first block covering a point writes it, points no block covers get 0.
-// The work is float64 arithmetic (this GPU's FP64 rate bounds it), within a few ulps of the
-// division form k_i + (k_{i+1} - k_i) ((nu - nu_i) / (nu_{i+1} - nu_i)); samples are exact.
+// Everything is float64, and this GPU's float64 rate (about two operations per clock per SM)
+// bounds both kernels, so they are built around doing few float64 operations per point.
+//
+// Uniform grid, two launches. k_cia_intervals (one thread per sample) decides which points
+// each interval holds exactly as the definition has it, on the rounded points
+// nu_j = nu_min + j dnu: interval [x_i, x_{i+1}) holds j in [c_i, c_{i+1}), c_i the first j
+// with nu_j >= x_i (a bracketed search around (x_i - nu_min) / dnu); the last sample holds
+// [c_{m-1}, e), e the first j with nu_j > x_last. It stores c_i, the interpolant at c_i,
+// k_i + (k_{i+1} - k_i) ((nu_{c_i} - x_i) / h_i), and its step per grid point,
+// (k_{i+1} - k_i) dnu / h_i (0 on the last sample). In k_cia_grid lane l of a warp takes
+// ROX_CIA_GRUN consecutive points, finds its interval by an integer search over c_i, and
+// from there adds the step once per point, taking the stored value afresh at each c_i: one
+// float64 addition per point, within ROX_CIA_GRUN ulps of the direct form and exact at
+// samples. The lane's run goes through shared memory so that the row is written with
+// coalesced stores.
+//
+// Nodes (k_cia): a warp takes a tile of 32 x ROX_CIA_RUN nodes, lane l the nodes
+// p0 + l + 32 s (coalesced stores); a lane finds the bracketing interval of its first node by
+// binary search and walks forward while the nodes increase (searching again if one goes
+// back), with the interval's reciprocal width formed once per interval.
+//
+// In both, the first block in input order that covers a point writes it; 0 where none does.
 #include <cstdio>
 #include <vector>
 #include "rox_internal.cuh"
@@ -96,8 +111,149 @@ __global__ void k_cia(const __grid_constant__ CiaArgs A, const double* __restric
   }
 }
 
+
+#define ROX_CIA_GRUN 32                      // consecutive grid points per lane
+#define ROX_CIA_GWARPS 4                     // warps per block
+#define ROX_CIA_GSTAGE (32 * (ROX_CIA_GRUN + 1))   // doubles per warp (padded against bank conflicts)
+
+struct CiaGrid {
+  double nu_min, dnu, inv_dnu;
+  long long n;
+};
+
+__device__ __forceinline__ double grid_nu(const CiaGrid& g, long long j) {
+  return __dadd_rn(g.nu_min, __dmul_rn((double)j, g.dnu));
+}
+
+// First j in [0, n] with nu_j >= x (strict: nu_j > x); nu_n counts as +infinity. The rounded
+// points never decrease in j, so a bisection over a bracket is exact; the bracket is
+// (x - nu_min) / dnu +- 4, widened to [0, n] on the side where it fails.
+__device__ long long grid_first(const CiaGrid& g, double x, bool strict) {
+  const double t = (x - g.nu_min) * g.inv_dnu;
+  long long c;
+  if (!(t > 0.0)) c = 0;
+  else if (t >= (double)g.n) c = g.n;
+  else c = (long long)ceil(t);
+  long long lo = c - 4 < 0 ? 0 : c - 4;
+  long long hi = c + 4 > g.n ? g.n : c + 4;
+  auto hit = [&](long long j) { const double v = grid_nu(g, j); return strict ? v > x : v >= x; };
+  if (lo > 0 && hit(lo - 1)) lo = 0;
+  if (hi < g.n && !hit(hi)) hi = g.n;
+  while (lo < hi) {
+    const long long mid = lo + ((hi - lo) >> 1);
+    if (hit(mid)) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Workspace of the uniform-grid path: per sample c_i (int64), the value at c_i and the step
+// (float64), per block e; unused for blocks whose temperature is not asked for.
+struct CiaTables {
+  long long* c;
+  double* v0;
+  double* dv;
+  long long* e;
+};
+
+__device__ __forceinline__ int block_of(const CiaArgs& A, long long q) {   // the block holding sample q
+  int lo = 0, hi = A.n_blocks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (A.off[mid] <= q) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_cia_intervals(const __grid_constant__ CiaArgs A, const double* __restrict__ nu,
+                                const double* __restrict__ k, const CiaGrid g, CiaTables T) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= A.off[A.n_blocks]) return;
+  const int b = block_of(A, q);
+  if (A.row[b] < 0) return;
+  const long long last = A.off[b + 1] - 1;
+  const double xi = nu[q];
+  const long long c = grid_first(g, xi, false);
+  T.c[q] = c;
+  if (q == last) {
+    T.v0[q] = k[q];
+    T.dv[q] = 0.0;
+    T.e[b] = grid_first(g, xi, true);
+  } else {
+    const double yi = k[q], dy = k[q + 1] - yi;
+    const double r = 1.0 / (nu[q + 1] - xi);
+    T.v0[q] = fma(dy, (grid_nu(g, c) - xi) * r, yi);
+    T.dv[q] = dy * (g.dnu * r);
+  }
+}
+
+__global__ void __launch_bounds__(32 * ROX_CIA_GWARPS)
+k_cia_grid(const __grid_constant__ CiaArgs A, const CiaGrid g, const CiaTables T, double* out) {
+  extern __shared__ double cia_stage[];
+  const int lane = threadIdx.x & 31;
+  double* st = cia_stage + (threadIdx.x >> 5) * ROX_CIA_GSTAGE + lane * (ROX_CIA_GRUN + 1);
+  const long long tile_pts = 32LL * ROX_CIA_GRUN;
+  const long long tiles_per_row = (g.n + tile_pts - 1) / tile_pts;
+  const long long n_tiles = (long long)A.n_rows * tiles_per_row;
+  const long long warps = (long long)gridDim.x * ROX_CIA_GWARPS;
+  for (long long tile = (long long)blockIdx.x * ROX_CIA_GWARPS + (threadIdx.x >> 5); tile < n_tiles; tile += warps) {
+    const int t = (int)(tile / tiles_per_row);
+    const long long p0 = (tile - (long long)t * tiles_per_row) * tile_pts;
+    const long long base = p0 + (long long)lane * ROX_CIA_GRUN;   // this lane's first point
+    const int n_run = (int)max(0LL, min((long long)ROX_CIA_GRUN, g.n - base));
+    unsigned long long done = 0;   // bit s: point base + s written
+    for (int b = 0; b < A.n_blocks; b++) {
+      if (A.row[b] != t) continue;
+      const long long o = A.off[b], m = A.off[b + 1] - A.off[b];
+      const long long* c = T.c + o;
+      const long long e = T.e[b];
+      const int s_lo = (int)max(0LL, min((long long)n_run, c[0] - base));
+      const int s_hi = (int)max(0LL, min((long long)n_run, e - base));
+      if (s_lo >= s_hi) continue;
+      long long j = base + s_lo;
+      long long i;
+      {   // the last interval starting at or before j (c_0 <= j < e here)
+        long long lo = 0, hi = m - 1;
+        while (lo < hi) {
+          const long long mid = (lo + hi + 1) >> 1;
+          if (c[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        i = lo;
+      }
+      double dval = T.dv[o + i];
+      double val = fma((double)(j - c[i]), dval, T.v0[o + i]);
+      long long nxt = i + 1 < m ? c[i + 1] : e;
+      for (int s = s_lo; s < s_hi; s++, j++) {
+        if (j >= nxt) {   // j is the first point of a later interval: take its stored value
+          do {
+            i++;
+            nxt = i + 1 < m ? c[i + 1] : e;
+          } while (j >= nxt && i < m - 1);
+          val = T.v0[o + i];
+          dval = T.dv[o + i];
+        }
+        if (!((done >> s) & 1ull)) st[s] = val;
+        val += dval;
+      }
+      const unsigned long long span = s_hi - s_lo >= 64 ? ~0ull : ((1ull << (s_hi - s_lo)) - 1ull);
+      done |= span << s_lo;
+    }
+    for (int s = 0; s < n_run; s++)
+      if (!((done >> s) & 1ull)) st[s] = 0.0;
+    __syncwarp();
+    // coalesced write-out: point p0 + q (q = c 32 + lane) sits at q + q / GRUN in the stage
+    const double* wst = cia_stage + (threadIdx.x >> 5) * ROX_CIA_GSTAGE;
+    double* row = out + (long long)t * g.n;
+#pragma unroll 4
+    for (int cc = 0; cc < ROX_CIA_GRUN; cc++) {
+      const int q = cc * 32 + lane;
+      if (p0 + q < g.n) row[p0 + q] = wst[q + q / ROX_CIA_GRUN];
+    }
+    __syncwarp();
+  }
+}
+
 int cia_launch(const rox_cia* cia, const double* nodes, double nu_min, double dnu, long long n, int n_T,
-               const double* T_out, double* out, cudaStream_t s) {
+               const double* T_out, double* out, void* ws, size_t ws_bytes, cudaStream_t s) {
   char msg[160];
   if (!cia || !cia->T_block || !cia->offset || !cia->nu || !cia->k) return rox_set_error(ROX_EINVAL, "cia arrays missing");
   if (cia->n_blocks < 1 || cia->n_blocks > ROX_CIA_MAX_BLOCKS) {
@@ -118,6 +274,32 @@ int cia_launch(const rox_cia* cia, const double* nodes, double nu_min, double dn
       if (T_out[t] == cia->T_block[b]) { A.row[b] = t; break; }
   }
   if (n <= 0) return ROX_OK;
+  if (!nodes) {
+    const size_t smem = sizeof(double) * ROX_CIA_GWARPS * ROX_CIA_GSTAGE;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_cia_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return rox_set_error(ROX_ECUDA, cudaGetErrorString(e));
+      attr = true;
+    }
+    CiaGrid g{nu_min, dnu, 1.0 / dnu, n};
+    const long long n_samples = A.off[A.n_blocks];
+    if (!ws || ((uintptr_t)ws & 7) || ws_bytes < rox_cia_workspace_size(A.n_blocks, n_samples))
+      return rox_set_error(ROX_EINVAL, "CIA workspace missing, misaligned or smaller than rox_cia_workspace_size");
+    CiaTables tb;
+    tb.c = (long long*)ws;
+    tb.v0 = (double*)(tb.c + n_samples);
+    tb.dv = tb.v0 + n_samples;
+    tb.e = (long long*)(tb.dv + n_samples);
+    k_cia_intervals<<<(unsigned)((n_samples + 255) / 256), 256, 0, s>>>(A, cia->nu, cia->k, g, tb);
+    const long long tiles = (long long)n_T * ((n + 32LL * ROX_CIA_GRUN - 1) / (32LL * ROX_CIA_GRUN));
+    long long blocks = (tiles + ROX_CIA_GWARPS - 1) / ROX_CIA_GWARPS;
+    if (blocks > 152 * 3 * 4) blocks = 152 * 3 * 4;
+    k_cia_grid<<<(int)blocks, 32 * ROX_CIA_GWARPS, smem, s>>>(A, g, tb, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rox_set_error(ROX_ECUDA, cudaGetErrorString(e));
+    return ROX_OK;
+  }
   const long long tiles = (long long)n_T * ((n + 32LL * ROX_CIA_RUN - 1) / (32LL * ROX_CIA_RUN));
   long long blocks = (tiles + 7) / 8;   // 8 warps per block, one tile per warp at a time
   if (blocks > 152 * 16) blocks = 152 * 16;
@@ -129,14 +311,20 @@ int cia_launch(const rox_cia* cia, const double* nodes, double nu_min, double dn
 
 }  // namespace
 
+extern "C" size_t rox_cia_workspace_size(int32_t n_blocks, int64_t n_samples) {
+  if (n_blocks < 0 || n_samples < 0) return 0;
+  return sizeof(double) * (3 * (size_t)n_samples + (size_t)n_blocks);
+}
+
 extern "C" int rox_cia_regrid(const rox_cia* cia, const rox_grid* grid, int n_T, const double* T_out, double* out,
-                              void* stream) {
+                              void* ws, size_t ws_bytes, void* stream) {
   if (!grid || !(grid->dnu > 0.0) || grid->n <= 0) return rox_set_error(ROX_EINVAL, "grid invalid");
-  return cia_launch(cia, nullptr, grid->nu_min, grid->dnu, grid->n, n_T, T_out, out, (cudaStream_t)stream);
+  return cia_launch(cia, nullptr, grid->nu_min, grid->dnu, grid->n, n_T, T_out, out, ws, ws_bytes,
+                    (cudaStream_t)stream);
 }
 
 extern "C" int rox_cia_regrid_nodes(const rox_cia* cia, const rox_nodes* nodes, int n_T, const double* T_out,
                                     double* out, void* stream) {
   if (!nodes || !nodes->nu || nodes->n <= 0) return rox_set_error(ROX_EINVAL, "nodes invalid");
-  return cia_launch(cia, nodes->nu, 0.0, 0.0, nodes->n, n_T, T_out, out, (cudaStream_t)stream);
+  return cia_launch(cia, nodes->nu, 0.0, 0.0, nodes->n, n_T, T_out, out, nullptr, 0, (cudaStream_t)stream);
 }
