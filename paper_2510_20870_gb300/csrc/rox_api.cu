@@ -16,7 +16,7 @@ cudaError_t rox_launch_widths(const rox_lines* L, double mass_amu, double P_bar,
                               float* gL, cudaStream_t s);
 cudaError_t rox_launch_strengths_multi(const rox_lines* L, int n_temps, const double* temps,
                                        const double* q_of_temp, double Q_ref, double* S_T,
-                                       unsigned long long* smax_bits, cudaStream_t s);
+                                       unsigned long long* smax_bits, bool exact, cudaStream_t s);
 cudaError_t rox_launch_scale_strengths(const double* S_T, long long n, int n_temps,
                                        const unsigned long long* smax_bits, float* S32, cudaStream_t s);
 cudaError_t rox_launch_windows(const double* nu0, long long n_lines, const rox_grid* g, double cutoff,
@@ -488,8 +488,10 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
                  : rox_launch_windows(lines->nu0, nl, grid, cutoff, nullptr, nullptr, nullptr, nullptr, w.geo,
                                       &w.hdr->evals_lines, &w.hdr->status, ROX_EUNSORTED, s);
     if ((rc = cuda_check(we, "windows kernel"))) return rc;
+    // a selection compares strengths against thresholds: there S(T) is the full FP64 form, so
+    // the kept set is decided on the same values as the definition's
     if ((rc = cuda_check(rox_launch_strengths_multi(lines, n_temps, temps.data(), qs.data(), Q_ref, w.S_T,
-                                                    w.hdr->smax_bits, s),
+                                                    w.hdr->smax_bits, sel != nullptr, s),
                          "strengths kernel")))
       return rc;
     const cudaError_t se =
@@ -671,7 +673,7 @@ int rox_line_select(const rox_lines* lines, const rox_grid* grid, double cutoff,
   if (nl == 0) return ok();
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = cuda_check(cudaMemsetAsync(w.hdr, 0, sizeof(RoxWsHeader), s), "memset"))) return rc;
-  if ((rc = cuda_check(rox_launch_strengths_multi(lines, 1, &T, &Q_T, Q_ref, w.S_T, w.hdr->smax_bits, s),
+  if ((rc = cuda_check(rox_launch_strengths_multi(lines, 1, &T, &Q_T, Q_ref, w.S_T, w.hdr->smax_bits, true, s),
                        "strengths kernel")))
     return rc;
   if ((rc = cuda_check(rox_launch_select(lines->nu0, w.S_T, nl, 1, w.hdr->smax_bits, origin, sel->bin_width, n_bins,

@@ -17,13 +17,13 @@ __device__ __forceinline__ double node_offset(double nu_min, double dnu, long lo
   return __dsub_rn(__dadd_rn(nu_min, __dmul_rn((double)j, dnu)), nu0);
 }
 
-// `guard` bounds, in index units, the rounding of the candidates (nu0 -/+ cutoff - nu_min)/dnu
+// `guard` bounds, in index units, the rounding of the candidates (nu0 - nu_min)/dnu -/+ cutoff/dnu
 // and of the cutoff test for every line within reach of the grid: a candidate farther than
 // that from an integer is the exact answer, and the exact test only runs for the others
 // (about one line in 1e6). Lines beyond reach end up clamped to an empty or edge window
 // either way.
 __global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, double nu_min,
-                          double dnu, double inv_dnu, double guard, long long n_grid, double cutoff,
+                          double dnu, double inv_dnu, double c_idx, double guard, long long n_grid, double cutoff,
                           int32_t* jlo_out, int32_t* jhi_out, int32_t* k0_out, float* f_out, float4* geo_out,
                           unsigned long long* evals_out, int32_t* unsorted_out, int32_t unsorted_value) {
   long long stride = (long long)gridDim.x * blockDim.x;
@@ -32,14 +32,16 @@ __global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, do
     double nu0 = nu0s[i];
     if (i > 0 && nu0s[i - 1] > nu0 && unsorted_out) *unsorted_out = unsorted_value;
     // first j with d_j >= -cutoff, last j with d_j <= cutoff (d_j non-decreasing in j): a
-    // candidate from a multiply by 1/dnu (within one index), then the exact test moves it
-    const double r_lo = (nu0 - cutoff - nu_min) * inv_dnu;
-    const double r_hi = (nu0 + cutoff - nu_min) * inv_dnu;
-    double lo_c = ceil(r_lo);
-    double hi_c = floor(r_hi);
-    lo_c = fmin(fmax(lo_c, -4.0), (double)n_grid + 4.0);
-    hi_c = fmin(fmax(hi_c, -4.0), (double)n_grid + 4.0);
-    long long jlo = (long long)lo_c, jhi = (long long)hi_c;
+    // candidate from the line centre in index units u = (nu0 - nu_min)/dnu -+ cutoff/dnu
+    // (within `guard` of the exact real), then the exact test moves it. The conversions round
+    // up / down straight to integers and saturate; a NaN centre gets an empty window.
+    double u = (nu0 - nu_min) * inv_dnu;
+    const double r_lo = u - c_idx;
+    const double r_hi = u + c_idx;
+    long long jlo = __double2ll_ru(r_lo), jhi = __double2ll_rd(r_hi);
+    jlo = jlo < -4 ? -4 : (jlo > n_grid + 4 ? n_grid + 4 : jlo);
+    jhi = jhi < -4 ? -4 : (jhi > n_grid + 4 ? n_grid + 4 : jhi);
+    if (isnan(u)) { jlo = -4; jhi = -4; u = 0.0; }
     if (!(fabs(r_lo - rint(r_lo)) > guard)) {
       for (int it = 0; it < 4 && node_offset(nu_min, dnu, jlo - 1, nu0) >= -cutoff; it++) jlo--;
       for (int it = 0; it < 4 && node_offset(nu_min, dnu, jlo, nu0) < -cutoff; it++) jlo++;
@@ -52,7 +54,6 @@ __global__ void k_windows(const double* __restrict__ nu0s, long long n_lines, do
     long long jh = jhi < -1 ? -1 : (jhi > n_grid - 1 ? n_grid - 1 : jhi);
     if (jh >= jl) ev += (unsigned long long)(jh - jl + 1);
     // centre decomposition (nu0 - nu_min)/dnu = k0 + f (k0 integer, f in [0, 1))
-    double u = (nu0 - nu_min) * inv_dnu;
     double k0 = floor(u);
     double f = u - k0;
     if (f >= 1.0) { k0 += 1.0; f -= 1.0; }
@@ -257,7 +258,8 @@ cudaError_t rox_launch_windows(const double* nu0, long long n_lines, const rox_g
   const double inv_dnu = 1.0 / g->dnu;
   const double nu_abs = fmax(fabs(g->nu_min), fabs(g->nu_min + (double)(g->n - 1) * g->dnu));
   const double guard = 16.0 * 2.3e-16 * ((nu_abs + 2.0 * cutoff) * inv_dnu + (double)g->n + 8.0);
-  k_windows<<<grid_for(n_lines), 256, 0, s>>>(nu0, n_lines, g->nu_min, g->dnu, inv_dnu, guard, g->n, cutoff, jlo, jhi,
+  k_windows<<<grid_for(n_lines), 256, 0, s>>>(nu0, n_lines, g->nu_min, g->dnu, inv_dnu, cutoff * inv_dnu, guard, g->n,
+                                               cutoff, jlo, jhi,
                                                k0,
                                                f, geo, evals, unsorted, unsorted_value);
   return cudaGetLastError();

@@ -33,6 +33,42 @@ __device__ __forceinline__ double line_strength(const StrengthConsts& k, double 
   return g_up * s_or_a / (8.0 * ROX_PI * ROX_C_CM * nu0 * nu0) * boltz * stim_T * k.q_ratio;
 }
 
+// The same S(T) with few FP64 operations, for the cross-section launches (this GPU runs
+// FP64 at about two operations per clock per SM, and FP64 exp, expm1 and a division cost
+// ~70 of them per line). Only the Boltzmann exponent needs FP64 range and accuracy: it is
+// formed in FP64 and split as a = k ln 2 + r (Cody and Waite's reduction with ln 2 in two
+// parts; the high part has 33 significant bits, so k * hi is exact for |k| < 2^20),
+// |r| <= ln(2)/2. exp(r), the stimulated-emission factor and the prefactor are FP32, and the
+// FP32 product (pre-scaled by 2^64 against underflow) is put back in range by the exact
+// powers 2^-64 and 2^k in FP64. Relative error a few 1e-7 (FP32 roundings), far below the
+// cross-section tolerance; exponents beyond +-700 and FP32 products beyond 2^+-100 (or zero,
+// or NaN) take the FP64 form.
+#define ROX_LN2_HI 0.6931471804855391       // ln 2 rounded to 33 significant bits
+#define ROX_LN2_LO 7.440617110012397e-11    // ln 2 - ROX_LN2_HI
+#define ROX_LOG2E 1.4426950408889634        // 1 / ln 2
+__device__ __forceinline__ double line_strength_fast(const StrengthConsts& k, double nu0, float s_or_a, float g_up,
+                                                     float e_lower) {
+  const double a = -(double)e_lower * k.c2_dT;
+  if (!(fabs(a) < 700.0)) return line_strength(k, nu0, (double)s_or_a, (double)g_up, (double)e_lower);
+  const double kd = rint(a * ROX_LOG2E);
+  const double r = fma(-kd, ROX_LN2_LO, fma(-kd, ROX_LN2_HI, a));
+  const float m = expf((float)r);
+  const float nu = (float)nu0;
+  const float stim = -expm1f(-(float)(ROX_C2 * k.inv_T) * nu);
+  float p;
+  if (k.convention == ROX_HITRAN) {
+    const float stim_ref = -expm1f(-(float)(ROX_C2 / ROX_T_REF) * nu);
+    p = (s_or_a * 0x1p64f) * (float)k.q_ratio * (stim / stim_ref);
+  } else {
+    p = (g_up * s_or_a) * ((float)(0x1p64 / (8.0 * ROX_PI * ROX_C_CM)) / (nu * nu)) * stim * (float)k.q_ratio;
+  }
+  const float pm = p * m;
+  if (!(fabsf(pm) >= 0x1p-100f && fabsf(pm) <= 0x1p100f))   // outside FP32's comfortable range (or 0, NaN)
+    return line_strength(k, nu0, (double)s_or_a, (double)g_up, (double)e_lower);
+  const double two_k = __longlong_as_double((long long)((int)kd + 1023) << 52);   // 2^k, |k| <= 1010
+  return (double)pm * 0x1p-64 * two_k;
+}
+
 __global__ void k_strengths(rox_lines L, StrengthConsts k, float* S_out) {
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) {
@@ -62,14 +98,16 @@ struct TempSet {
   StrengthConsts k[ROX_MAX_PT];
 };
 
+template <bool FAST>
 __global__ void k_strengths_multi(rox_lines L, TempSet ts,
                                   double* S_T, unsigned long long* smax_bits) {
   long long stride = (long long)gridDim.x * blockDim.x;
   for (int t = 0; t < ts.n; t++) {
     double mx = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) {
-      double g = (L.convention == ROX_EXOMOL) ? (double)L.g_up[i] : 1.0;
-      double s = line_strength(ts.k[t], L.nu0[i], (double)L.s_or_a[i], g, (double)L.e_lower[i]);
+      const float g = (L.convention == ROX_EXOMOL) ? L.g_up[i] : 1.0f;
+      const double s = FAST ? line_strength_fast(ts.k[t], L.nu0[i], L.s_or_a[i], g, L.e_lower[i])
+                            : line_strength(ts.k[t], L.nu0[i], (double)L.s_or_a[i], (double)g, (double)L.e_lower[i]);
       S_T[(long long)t * L.n + i] = s;
       mx = fmax(mx, s);
     }
@@ -222,8 +260,8 @@ __global__ void k_strengths_jobs(const __grid_constant__ RoxStrengthJobs J) {
     double mx = 0.0;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < jb.count; t += stride) {
       const long long i = jb.l0 + t;
-      const double g = (L.convention == ROX_EXOMOL) ? (double)L.g_up[i] : 1.0;
-      const double sv = line_strength(k, L.nu0[i], (double)L.s_or_a[i], g, (double)L.e_lower[i]);
+      const float g = (L.convention == ROX_EXOMOL) ? L.g_up[i] : 1.0f;
+      const double sv = line_strength_fast(k, L.nu0[i], L.s_or_a[i], g, L.e_lower[i]);
       jb.S64[t] = sv;
       mx = fmax(mx, sv);
     }
@@ -282,11 +320,14 @@ cudaError_t rox_launch_widths(const rox_lines* L, double mass_amu, double P_bar,
 
 cudaError_t rox_launch_strengths_multi(const rox_lines* L, int n_temps, const double* temps,
                                        const double* q_of_temp, double Q_ref, double* S_T,
-                                       unsigned long long* smax_bits, cudaStream_t s) {
+                                       unsigned long long* smax_bits, bool exact, cudaStream_t s) {
   TempSet ts;
   ts.n = n_temps;
   for (int t = 0; t < n_temps; t++) ts.k[t] = make_consts(L->convention, temps[t], q_of_temp[t], Q_ref);
-  k_strengths_multi<<<grid_for(L->n), 256, 0, s>>>(*L, ts, S_T, smax_bits);
+  if (exact)
+    k_strengths_multi<false><<<grid_for(L->n), 256, 0, s>>>(*L, ts, S_T, smax_bits);
+  else
+    k_strengths_multi<true><<<grid_for(L->n), 256, 0, s>>>(*L, ts, S_T, smax_bits);
   return cudaGetLastError();
 }
 

@@ -86,9 +86,10 @@ def test_selected_cross_sections():
 
 
 def test_rel_zero_equals_unselected():
-    """rel = 0 keeps every line that reaches the grid: the unselected result (the kept-line
-    index then lists every line the spans reach, in the same order, so the sums agree to the
-    last bit in practice; the check allows rounding)."""
+    """rel = 0 keeps every line that reaches the grid: the unselected result. The kept-line
+    index then lists every line the spans reach, in the same order; the selection takes S(T) in
+    the full FP64 form (it decides the kept set) and the plain launch in the reduced form, so
+    the two agree to a few 1e-7."""
     w = rs.CONFIGS[1]
     L = oracle.sort_lines(rs.make_lines(w))
     grid = rs.grid_of(w)
