@@ -39,6 +39,8 @@ struct CiaArgs {
   int32_t n_rows;
   long long off[ROX_CIA_MAX_BLOCKS + 1];   // block b: samples off[b] .. off[b+1]-1
   int32_t row[ROX_CIA_MAX_BLOCKS];         // output row of block b, -1 if its temperature is not asked for
+  int32_t row_start[ROX_CIA_MAX_TEMPS + 1];   // the blocks of row t: row_block[row_start[t] .. row_start[t+1]-1]
+  int16_t row_block[ROX_CIA_MAX_BLOCKS];      // block indices grouped by row, input order within a row
 };
 
 #define ROX_CIA_RUN 32
@@ -61,8 +63,8 @@ __global__ void k_cia(const __grid_constant__ CiaArgs A, const double* __restric
     const long long p0 = (tile - (long long)t * tiles_per_row) * tile_pts + lane;
     double* row = out + (long long)t * n;
     unsigned done = 0;   // bit s: point p0 + 32 s written
-    for (int b = 0; b < A.n_blocks; b++) {
-      if (A.row[b] != t) continue;
+    for (int q = A.row_start[t]; q < A.row_start[t + 1]; q++) {
+      const int b = A.row_block[q];
       const long long o = A.off[b], m = A.off[b + 1] - A.off[b];
       const double* x = nu + o;
       const double* y = k + o;
@@ -201,8 +203,8 @@ k_cia_grid(const __grid_constant__ CiaArgs A, const CiaGrid g, const CiaTables T
     const long long base = p0 + (long long)lane * ROX_CIA_GRUN;   // this lane's first point
     const int n_run = (int)max(0LL, min((long long)ROX_CIA_GRUN, g.n - base));
     unsigned long long done = 0;   // bit s: point base + s written
-    for (int b = 0; b < A.n_blocks; b++) {
-      if (A.row[b] != t) continue;
+    for (int q = A.row_start[t]; q < A.row_start[t + 1]; q++) {
+      const int b = A.row_block[q];
       const long long o = A.off[b], m = A.off[b + 1] - A.off[b];
       const long long* c = T.c + o;
       const long long e = T.e[b];
@@ -266,12 +268,21 @@ int cia_launch(const rox_cia* cia, const double* nodes, double nu_min, double dn
   A.n_rows = n_T;
   A.off[0] = cia->offset[0];
   if (A.off[0] != 0) return rox_set_error(ROX_EINVAL, "cia->offset[0] must be 0");
+  for (int t = 0; t <= n_T; t++) A.row_start[t] = 0;
   for (int b = 0; b < cia->n_blocks; b++) {
     A.off[b + 1] = cia->offset[b + 1];
     if (A.off[b + 1] <= A.off[b]) return rox_set_error(ROX_EINVAL, "every CIA block needs at least one sample");
     A.row[b] = -1;
     for (int t = 0; t < n_T; t++)
       if (T_out[t] == cia->T_block[b]) { A.row[b] = t; break; }
+    if (A.row[b] >= 0) A.row_start[A.row[b] + 1]++;
+  }
+  for (int t = 0; t < n_T; t++) A.row_start[t + 1] += A.row_start[t];
+  {
+    int fill[ROX_CIA_MAX_TEMPS];
+    for (int t = 0; t < n_T; t++) fill[t] = A.row_start[t];
+    for (int b = 0; b < cia->n_blocks; b++)
+      if (A.row[b] >= 0) A.row_block[fill[A.row[b]]++] = (int16_t)b;
   }
   if (n <= 0) return ROX_OK;
   if (!nodes) {
