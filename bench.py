@@ -34,7 +34,7 @@ import rox_synth as rs  # noqa: E402
 FLOPS_PER_EVAL = 11.0   # far-wing pair formula: 10 FFMA + 2 FMUL per 2 evaluations (+ 1 MUFU rcp)
 # DRAM bytes per Voigt launch on the full exomol workload: ncu dram__bytes_read + write of the
 # 2e6-line case (profiles/k_voigt_exomol_2e6lines.md), scaled by evaluations (x5.0)
-VOIGT_TRAFFIC_BYTES = 3.035e8
+VOIGT_TRAFFIC_BYTES = 3.037e8
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "Voigt line-profile evals/s"
@@ -710,6 +710,20 @@ def run_cia(args):
     ms = e0.elapsed_time(e1) / args.steps
     points = len(temps) * grid[2]
     out_bytes = points * 8
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle (numpy, one thread) on every fifth temperature over the whole grid
+        import oracle
+        nodes = oracle.grid_nodes(*grid)
+        pick = temps[::5]
+        per_nu = [nu_h[off[b]:off[b + 1]] for b in range(len(Tb))]
+        per_k = [k_h[off[b]:off[b + 1]] for b in range(len(Tb))]
+        t0 = time.perf_counter()
+        oracle.cia_regrid(Tb, per_nu, per_k, pick, nodes)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(pick) * grid[2] / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+               "sample": "%d of the %d temperatures over all %d points (numpy, one thread), %.1f s" % (
+                   len(pick), len(temps), grid[2], dt)}
     peak = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) else 6800.0
     achieved = out_bytes / (ms * 1e-3) / 1e9
@@ -724,7 +738,7 @@ def run_cia(args):
                                    "frac": achieved / peak, "traffic": None,
                                    "note": "algorithmic bytes: the float64 output written once (inputs %.1f MB, "
                                            "L2-resident)" % ((nu_h.size * 16) / 1e6)},
-                      "gpu_launches": 2 * args.steps, "clocks": clocks.summary()}))
+                      "gpu_launches": 2 * args.steps, "clocks": clocks.summary(), "cpu_baseline": cpu}))
 
 
 def main():
