@@ -4,8 +4,10 @@
 // coefficients read from the input files are restructured into a wavelength- and
 // temperature-dependent grid.
 //
-// Everything is float64, and this GPU's float64 rate (about two operations per clock per SM)
-// bounds both kernels, so they are built around doing few float64 operations per point.
+// Everything is float64, and this GPU's float64 rate is low (about two operations per clock
+// per SM), so both kernels are built around doing few float64 operations per point; what
+// bounds the grid kernel then is the latency of its table reads, hence short tiles and many
+// warps.
 //
 // Uniform grid, two launches. k_cia_intervals (one thread per sample) decides which points
 // each interval holds exactly as the definition has it, on the rounded points
@@ -13,12 +15,12 @@
 // with nu_j >= x_i (a bracketed search around (x_i - nu_min) / dnu); the last sample holds
 // [c_{m-1}, e), e the first j with nu_j > x_last. It stores c_i, the interpolant at c_i,
 // k_i + (k_{i+1} - k_i) ((nu_{c_i} - x_i) / h_i), and its step per grid point,
-// (k_{i+1} - k_i) dnu / h_i (0 on the last sample). In k_cia_grid lane l of a warp takes
-// ROX_CIA_GRUN consecutive points, finds its interval by an integer search over c_i, and
-// from there adds the step once per point, taking the stored value afresh at each c_i: one
-// float64 addition per point, within ROX_CIA_GRUN ulps of the direct form and exact at
-// samples. The lane's run goes through shared memory so that the row is written with
-// coalesced stores.
+// (k_{i+1} - k_i) dnu / h_i (0 on the last sample). In k_cia_grid a warp takes 32 x
+// ROX_CIA_GRUN consecutive points of a row, lane l the points p0 + l + 32 s, so every store
+// is coalesced; the interval of the tile's first point comes from a warp-parallel integer
+// search over c_i (32 probes a round), each lane walks on from there, evaluates the interpolant at its first point of an
+// interval (k(c_i) + (j - c_i) step) and then adds 32 steps per point: one float64 addition
+// per point, within ROX_CIA_GRUN roundings of the direct form and exact at samples.
 //
 // Nodes (k_cia): a warp takes a tile of 32 x ROX_CIA_RUN nodes, lane l the nodes
 // p0 + l + 32 s (coalesced stores); a lane finds the bracketing interval of its first node by
@@ -114,9 +116,8 @@ __global__ void k_cia(const __grid_constant__ CiaArgs A, const double* __restric
 }
 
 
-#define ROX_CIA_GRUN 32                      // consecutive grid points per lane
+#define ROX_CIA_GRUN 16                      // points per lane in a tile (tile: 32 x GRUN consecutive points)
 #define ROX_CIA_GWARPS 4                     // warps per block
-#define ROX_CIA_GSTAGE (32 * (ROX_CIA_GRUN + 1))   // doubles per warp (padded against bank conflicts)
 
 struct CiaGrid {
   double nu_min, dnu, inv_dnu;
@@ -190,9 +191,7 @@ __global__ void k_cia_intervals(const __grid_constant__ CiaArgs A, const double*
 
 __global__ void __launch_bounds__(32 * ROX_CIA_GWARPS)
 k_cia_grid(const __grid_constant__ CiaArgs A, const CiaGrid g, const CiaTables T, double* out) {
-  extern __shared__ double cia_stage[];
   const int lane = threadIdx.x & 31;
-  double* st = cia_stage + (threadIdx.x >> 5) * ROX_CIA_GSTAGE + lane * (ROX_CIA_GRUN + 1);
   const long long tile_pts = 32LL * ROX_CIA_GRUN;
   const long long tiles_per_row = (g.n + tile_pts - 1) / tile_pts;
   const long long n_tiles = (long long)A.n_rows * tiles_per_row;
@@ -200,57 +199,57 @@ k_cia_grid(const __grid_constant__ CiaArgs A, const CiaGrid g, const CiaTables T
   for (long long tile = (long long)blockIdx.x * ROX_CIA_GWARPS + (threadIdx.x >> 5); tile < n_tiles; tile += warps) {
     const int t = (int)(tile / tiles_per_row);
     const long long p0 = (tile - (long long)t * tiles_per_row) * tile_pts;
-    const long long base = p0 + (long long)lane * ROX_CIA_GRUN;   // this lane's first point
-    const int n_run = (int)max(0LL, min((long long)ROX_CIA_GRUN, g.n - base));
-    unsigned long long done = 0;   // bit s: point base + s written
+    const long long p_end = min(p0 + tile_pts, g.n);
+    double* row = out + (long long)t * g.n;
+    unsigned done = 0;   // bit s: point p0 + lane + 32 s written
     for (int q = A.row_start[t]; q < A.row_start[t + 1]; q++) {
       const int b = A.row_block[q];
       const long long o = A.off[b], m = A.off[b + 1] - A.off[b];
       const long long* c = T.c + o;
       const long long e = T.e[b];
-      const int s_lo = (int)max(0LL, min((long long)n_run, c[0] - base));
-      const int s_hi = (int)max(0LL, min((long long)n_run, e - base));
-      if (s_lo >= s_hi) continue;
-      long long j = base + s_lo;
+      const long long a = max(c[0], p0), z = min(e, p_end);   // the block's points in this tile: [a, z)
+      if (a >= z) continue;
       long long i;
-      {   // the last interval starting at or before j (c_0 <= j < e here)
-        long long lo = 0, hi = m - 1;
-        while (lo < hi) {
-          const long long mid = (lo + hi + 1) >> 1;
-          if (c[mid] <= j) lo = mid; else hi = mid - 1;
+      {   // the last interval starting at or before a (c_0 <= a): 32 probes a round, one per
+          // lane, narrow the range 32-fold (three dependent loads up to 32768 samples)
+        long long lo = 0, len = m;
+        while (len > 1) {
+          const long long step = (len + 31) >> 5;
+          const long long off = (long long)lane * step;
+          const bool le = off < len && c[lo + off] <= a;
+          const int k = __popc(__ballot_sync(0xffffffffu, le));   // probes 0 .. k-1 are <= a
+          const long long nlo = lo + (long long)(k - 1) * step;
+          len = min(step, lo + len - nlo);
+          lo = nlo;
         }
         i = lo;
       }
-      double dval = T.dv[o + i];
-      double val = fma((double)(j - c[i]), dval, T.v0[o + i]);
-      long long nxt = i + 1 < m ? c[i + 1] : e;
-      for (int s = s_lo; s < s_hi; s++, j++) {
-        if (j >= nxt) {   // j is the first point of a later interval: take its stored value
-          do {
+      const long long d_lo = a - p0 - lane, d_hi = z - p0 - lane;
+      const int s_lo = d_lo > 0 ? (int)((d_lo + 31) >> 5) : 0;   // first s with p0 + lane + 32 s >= a
+      const int s_hi = d_hi > 0 ? (int)((d_hi + 31) >> 5) : 0;   // ... >= z
+      long long j = p0 + lane + 32LL * s_lo;
+      long long nxt = -1;   // forces the set-up at the lane's first point
+      double val = 0.0, step = 0.0;
+      for (int s = s_lo; s < s_hi; s++, j += 32) {
+        if (j >= nxt) {   // first point of the lane in this block, or a later interval
+          nxt = i + 1 < m ? c[i + 1] : e;
+          while (j >= nxt && i < m - 1) {
             i++;
             nxt = i + 1 < m ? c[i + 1] : e;
-          } while (j >= nxt && i < m - 1);
-          val = T.v0[o + i];
-          dval = T.dv[o + i];
+          }
+          const double dv = T.dv[o + i];
+          val = fma((double)(j - c[i]), dv, T.v0[o + i]);
+          step = 32.0 * dv;
         }
-        if (!((done >> s) & 1ull)) st[s] = val;
-        val += dval;
+        if (!((done >> s) & 1u)) row[j] = val;
+        val += step;
       }
-      const unsigned long long span = s_hi - s_lo >= 64 ? ~0ull : ((1ull << (s_hi - s_lo)) - 1ull);
-      done |= span << s_lo;
+      if (s_hi > s_lo) done |= (s_hi - s_lo >= 32 ? ~0u : ((1u << (s_hi - s_lo)) - 1u)) << s_lo;
     }
-    for (int s = 0; s < n_run; s++)
-      if (!((done >> s) & 1ull)) st[s] = 0.0;
-    __syncwarp();
-    // coalesced write-out: point p0 + q (q = c 32 + lane) sits at q + q / GRUN in the stage
-    const double* wst = cia_stage + (threadIdx.x >> 5) * ROX_CIA_GSTAGE;
-    double* row = out + (long long)t * g.n;
-#pragma unroll 4
-    for (int cc = 0; cc < ROX_CIA_GRUN; cc++) {
-      const int q = cc * 32 + lane;
-      if (p0 + q < g.n) row[p0 + q] = wst[q + q / ROX_CIA_GRUN];
+    for (int s = 0; s < ROX_CIA_GRUN; s++) {
+      const long long j = p0 + lane + 32LL * s;
+      if (j < p_end && !((done >> s) & 1u)) row[j] = 0.0;
     }
-    __syncwarp();
   }
 }
 
@@ -286,13 +285,6 @@ int cia_launch(const rox_cia* cia, const double* nodes, double nu_min, double dn
   }
   if (n <= 0) return ROX_OK;
   if (!nodes) {
-    const size_t smem = sizeof(double) * ROX_CIA_GWARPS * ROX_CIA_GSTAGE;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_cia_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return rox_set_error(ROX_ECUDA, cudaGetErrorString(e));
-      attr = true;
-    }
     CiaGrid g{nu_min, dnu, 1.0 / dnu, n};
     const long long n_samples = A.off[A.n_blocks];
     if (!ws || ((uintptr_t)ws & 7) || ws_bytes < rox_cia_workspace_size(A.n_blocks, n_samples))
@@ -305,8 +297,8 @@ int cia_launch(const rox_cia* cia, const double* nodes, double nu_min, double dn
     k_cia_intervals<<<(unsigned)((n_samples + 255) / 256), 256, 0, s>>>(A, cia->nu, cia->k, g, tb);
     const long long tiles = (long long)n_T * ((n + 32LL * ROX_CIA_GRUN - 1) / (32LL * ROX_CIA_GRUN));
     long long blocks = (tiles + ROX_CIA_GWARPS - 1) / ROX_CIA_GWARPS;
-    if (blocks > 152 * 3 * 4) blocks = 152 * 3 * 4;
-    k_cia_grid<<<(int)blocks, 32 * ROX_CIA_GWARPS, smem, s>>>(A, g, tb, out);
+    if (blocks > 152 * 12 * 8) blocks = 152 * 12 * 8;
+    k_cia_grid<<<(int)blocks, 32 * ROX_CIA_GWARPS, 0, s>>>(A, g, tb, out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return rox_set_error(ROX_ECUDA, cudaGetErrorString(e));
     return ROX_OK;
