@@ -35,6 +35,9 @@ FLOPS_PER_EVAL = 11.0   # far-wing pair formula: 10 FFMA + 2 FMUL per 2 evaluati
 # DRAM bytes per Voigt launch on the full exomol workload: ncu dram__bytes_read + write of the
 # 2e6-line case (profiles/k_voigt_exomol_2e6lines.md), scaled by evaluations (x5.0)
 VOIGT_TRAFFIC_BYTES = 3.037e8
+# DRAM bytes of one k_cia_grid launch on the CIA workload (ncu dram__bytes_read + write,
+# profiles/k_cia_grid_40T_2970001pts.md; part of the 950 MB output is still in L2 at the end)
+CIA_TRAFFIC_BYTES = 9.086e8
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "Voigt line-profile evals/s"
@@ -736,9 +739,11 @@ def run_cia(args):
                                                                                    grid[2]),
                                  "l2": "output %.0f MB per step, larger than L2" % (out_bytes / 1e6)},
                       "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                   "frac": achieved / peak, "traffic": None,
+                                   "frac": achieved / peak, "traffic": CIA_TRAFFIC_BYTES, "kernel": "k_cia_grid",
+                                   "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                                    "note": "algorithmic bytes: the float64 output written once (inputs %.1f MB, "
-                                           "L2-resident)" % ((nu_h.size * 16) / 1e6)},
+                                           "L2-resident), over the whole step (per-sample interval pass + "
+                                           "grid kernel)" % ((nu_h.size * 16) / 1e6)},
                       "gpu_launches": 2 * args.steps, "clocks": clocks.summary(), "cpu_baseline": cpu}))
 
 
