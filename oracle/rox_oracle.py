@@ -10,7 +10,7 @@ Paper: pyROX (de Regt et al.), section "Functionality of pyROX":
     (Gandhi et al. 2020, Eq. 12), computed with scipy.special.wofz. That routine is
     the one used here.
   * "Combine and save": profiles summed into a cross-section per (P,T).
-Readings where the paper is silent (all listed in the design doc as well):
+Readings where the paper is silent:
   R1  constants CODATA 2018; T_ref = 296 K; pressures in bar, P_ref = 1 atm = 1.01325 bar.
   R2  HITRAN strength  S(T) = S_ref * Q(T_ref)/Q(T) * exp(-c2 E''(1/T - 1/T_ref))
                              * (1 - exp(-c2 nu0/T)) / (1 - exp(-c2 nu0/T_ref)).
