@@ -726,6 +726,31 @@ def run_cia(args):
     ms = e0.elapsed_time(e1) / args.steps
     points = len(temps) * grid[2]
     out_bytes = points * 8
+    e2e = None
+    if not args.no_e2e:
+        # through the public call from pinned host memory: the blocks in, the rows out, every step
+        nu_p = torch.from_numpy(nu_h).pin_memory()
+        k_p = torch.from_numpy(k_h).pin_memory()
+        out_p = torch.empty(out.shape, dtype=torch.float64).pin_memory()
+        n_e2e = max(3, min(args.steps, 50))
+
+        def e2e_step():
+            nu.copy_(nu_p, non_blocking=True)
+            k.copy_(k_p, non_blocking=True)
+            rox.rox_cia_regrid(Tb, off, nu, k, grid, temps, out, ws)
+            out_p.copy_(out, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n_e2e):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_e = e0.elapsed_time(e1) / n_e2e
+        assert np.array_equal(out_p.numpy(), out.cpu().numpy())
+        e2e = {"value": points / (ms_e * 1e-3), "unit": "points/s", "h2d_bytes_per_step": int(nu_h.nbytes + k_h.nbytes),
+               "d2h_bytes_per_step": int(out_bytes), "ms_per_step": ms_e, "steps": n_e2e,
+               "includes": "H2D of the blocks from pinned memory, rox_cia_regrid, D2H of all rows to pinned memory"}
     cpu = None
     if not args.no_cpu_baseline:
         # the oracle (numpy, one thread): the whole workload, repeated for about 10 s
@@ -757,7 +782,7 @@ def run_cia(args):
                                    "note": "algorithmic bytes: the float64 output written once (inputs %.1f MB, "
                                            "L2-resident), over the whole step (per-sample interval pass + "
                                            "grid kernel)" % ((nu_h.size * 16) / 1e6)},
-                      "gpu_launches": 2 * args.steps, "clocks": clocks.summary(), "cpu_baseline": cpu}))
+                      "gpu_launches": 2 * args.steps, "clocks": clocks.summary(), "cpu_baseline": cpu, "e2e": e2e}))
 
 
 def main():
