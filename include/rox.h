@@ -293,7 +293,8 @@ int rox_node_windows(const double* nu0_sorted, int64_t n_lines, const rox_nodes*
  * temperature T_block[b] (HOST) with samples offset[b] .. offset[b+1]-1 (offset HOST, [n_blocks+1],
  * offset[0] = 0, at least one sample per block) of the DEVICE arrays nu (cm^-1, strictly
  * increasing within a block; not checked) and k (coefficients, any unit). Output: out
- * [n_T][n] double (DEVICE), row t for temperature T_out[t] (HOST, n_T <= ROX_CIA_MAX_TEMPS) on the
+ * [n_T][n] double (DEVICE), row t for temperature T_out[t] (HOST, n_T <= ROX_CIA_MAX_TEMPS, finite
+ * and distinct) on the
  * grid's points (nu_min + j dnu, one multiply and one add, or the given nodes): at each point
  * the first block (input order) with T_block == T_out[t] whose sample range contains it, linearly
  * interpolated between its bracketing samples, k_i + (k_{i+1} - k_i) (nu - nu_i) / (nu_{i+1} - nu_i),

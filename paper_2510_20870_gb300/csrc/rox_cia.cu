@@ -28,6 +28,8 @@
 // back), with the interval's reciprocal width formed once per interval.
 //
 // In both, the first block in input order that covers a point writes it; 0 where none does.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <vector>
 #include "rox_internal.cuh"
@@ -262,6 +264,14 @@ int cia_launch(const rox_cia* cia, const double* nodes, double nu_min, double dn
     return rox_set_error(ROX_EINVAL, msg);
   }
   if (n_T < 1 || n_T > ROX_CIA_MAX_TEMPS || !T_out || !out) return rox_set_error(ROX_EINVAL, "n_T, T_out or out invalid");
+  {   // output temperatures: finite and distinct (each block feeds at most one row)
+    std::vector<double> Ts(T_out, T_out + n_T);
+    for (double v : Ts)
+      if (!std::isfinite(v)) return rox_set_error(ROX_EINVAL, "T_out holds a non-finite temperature");
+    std::sort(Ts.begin(), Ts.end());
+    for (int t = 1; t < n_T; t++)
+      if (Ts[t] == Ts[t - 1]) return rox_set_error(ROX_EINVAL, "T_out holds a temperature twice");
+  }
   static thread_local CiaArgs A;
   A.n_blocks = cia->n_blocks;
   A.n_rows = n_T;

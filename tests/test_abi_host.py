@@ -88,3 +88,37 @@ def test_static_scratch_holds_the_largest_static_problem():
     from paper_2510_20870_gb300 import _binding as b
     need = b.rox_xsec_workspace_size(262144, (0.0, 0.01, 1 << 21), 1)
     assert 0 < need <= 16 << 20, need
+
+
+def test_cia_arguments_rejected_on_host(lib):
+    """CIA restructuring: every malformed layout is refused before anything reaches the GPU
+    (the device pointers here are placeholders that are never dereferenced)."""
+    L = lib.lib
+    assert L.rox_cia_workspace_size(2, 10) == 8 * (3 * 10 + 2)
+
+    def call(T_block, offset, T_out, grid=(0.0, 1.0, 10), ws=256, ws_bytes=1 << 20, nodes=None):
+        tb = (ctypes.c_double * max(1, len(T_block)))(*T_block)
+        off = (ctypes.c_int64 * len(offset))(*offset)
+        to = (ctypes.c_double * max(1, len(T_out)))(*T_out)
+        C = lib.RoxCia(len(T_block), 0, ctypes.cast(tb, ctypes.c_void_p), ctypes.cast(off, ctypes.c_void_p), 8, 8)
+        if nodes is not None:
+            N = lib.RoxNodes(*nodes)
+            return L.rox_cia_regrid_nodes(ctypes.byref(C), ctypes.byref(N), len(T_out), to, 8, None)
+        G = lib.RoxGrid(*grid)
+        return L.rox_cia_regrid(ctypes.byref(C), ctypes.byref(G), len(T_out), to, 8, ws, ws_bytes, None)
+
+    E = lib.ROX_EINVAL
+    assert call([], [0], [300.0]) == E                                   # no block
+    assert call([300.0], [1, 4], [300.0]) == E                           # offset[0] != 0
+    assert call([300.0, 500.0], [0, 3, 3], [300.0]) == E                 # an empty block
+    assert call([300.0], [0, 4], [300.0, 300.0]) == E and b"twice" in L.rox_last_error()
+    assert call([300.0], [0, 4], [float("nan")]) == E
+    assert call([300.0], [0, 4], []) == E                                # no output row
+    assert call([300.0], [0, 4], [float(t) for t in range(1, 4098)]) == E   # more rows than ROX_CIA_MAX_TEMPS
+    assert call([300.0], [0, 4], [300.0], grid=(0.0, -1.0, 10)) == E     # dnu <= 0
+    assert call([300.0], [0, 4], [300.0], grid=(0.0, 1.0, 0)) == E       # no point
+    need = L.rox_cia_workspace_size(1, 4)
+    assert call([300.0], [0, 4], [300.0], ws_bytes=need - 8) == E        # workspace one element short
+    assert call([300.0], [0, 4], [300.0], ws=260, ws_bytes=need) == E    # workspace not 8-byte aligned
+    assert call([300.0], [0, 4], [300.0], ws=None, ws_bytes=need) == E   # no workspace
+    assert call([300.0], [0, 4], [300.0], nodes=(None, 10)) == E         # nodes missing
