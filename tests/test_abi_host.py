@@ -122,3 +122,60 @@ def test_cia_arguments_rejected_on_host(lib):
     assert call([300.0], [0, 4], [300.0], ws=260, ws_bytes=need) == E    # workspace not 8-byte aligned
     assert call([300.0], [0, 4], [300.0], ws=None, ws_bytes=need) == E   # no workspace
     assert call([300.0], [0, 4], [300.0], nodes=(None, 10)) == E         # nodes missing
+
+
+def test_extension_arguments_rejected_on_host(lib):
+    """Selection, broadening descriptions and user-provided nodes: malformed arguments are
+    refused on the host with the documented codes (device pointers are placeholders)."""
+    L = lib.lib
+    by = ctypes.byref
+    G = lib.RoxGrid(2000.0, 0.01, 50001)
+    hit = lib.RoxLines(nu0=8, s_or_a=8, g_up=None, e_lower=8, gamma_ref=8, n_t=8, n=10, convention=0, width_dtype=0)
+    exo = lib.RoxLines(nu0=8, s_or_a=8, g_up=8, e_lower=8, gamma_ref=8, n_t=8, n=10, convention=1, width_dtype=0)
+    P, T, Q = (ctypes.c_double * 1)(1.0), (ctypes.c_double * 1)(1000.0), (ctypes.c_double * 1)(1.0)
+    E = lib.ROX_EINVAL
+
+    # main-contributor selection: rel >= 0, bin_width > 0, bins within ROX_MAX_SELECT_BINS
+    for rel, bw in ((-1.0, 1.0), (float("nan"), 1.0), (1e-3, 0.0), (1e-3, -2.0), (1e-3, 1e-9)):
+        sel = lib.RoxSelect(rel, bw)
+        assert L.rox_xsec_select_workspace_size(10, by(G), 1, 25.0, by(sel)) == 0, (rel, bw)
+        rc = L.rox_xsec_select_batch(by(hit), by(G), 1, P, T, Q, 1.0, 18.0, 25.0, 0, by(sel), 8, 256, 1 << 30, None)
+        assert rc in (E, lib.ROX_ERANGE), (rel, bw, rc)
+    assert L.rox_xsec_select_batch(by(hit), by(G), 1, P, T, Q, 1.0, 18.0, 25.0, 0, None, 8, 256, 1 << 30, None) == E
+
+    # broadening descriptions
+    def broad(n_b, vmr=(1.0,), cols=True, natural=0, table=False, j_lower=None, table_len=0):
+        br = lib.RoxBroadening()
+        br.n_broadeners, br.natural, br.table_len = n_b, natural, table_len
+        br.j_lower = j_lower
+        for b in range(min(n_b, 4)):
+            br.vmr[b] = vmr[b] if b < len(vmr) else 0.5
+            if table:
+                br.table_gamma[b], br.table_n[b] = 8, 8
+            elif cols:
+                br.gamma_ref[b], br.n_t[b] = 8, 8
+        return br
+
+    def xsec(lines, br):
+        return L.rox_xsec_broadened_batch(by(lines), by(G), by(br), 1, P, T, Q, 1.0, 18.0, 25.0, 0, 8, 256, 1 << 30,
+                                          None)
+    assert L.rox_xsec_broadened_batch(by(hit), by(G), None, 1, P, T, Q, 1.0, 18.0, 25.0, 0, 8, 256, 1 << 30,
+                                      None) == E
+    assert xsec(hit, broad(0)) == E                                  # no broadener
+    assert xsec(hit, broad(5)) == E                                  # more than ROX_MAX_BROADENERS
+    assert xsec(hit, broad(1, vmr=(-0.5,))) == E                     # negative mixing ratio
+    assert xsec(hit, broad(1, cols=False)) == E                      # neither columns nor a table
+    assert xsec(hit, broad(1, natural=1)) == E                       # natural width needs Einstein A
+    assert xsec(exo, broad(1, table=True, table_len=0, j_lower=8)) == E    # empty J table
+    assert xsec(exo, broad(1, table=True, table_len=60, j_lower=None)) == E  # table without J''
+    out = (ctypes.c_float * 10)()
+    assert L.rox_lorentz_widths(by(hit), by(broad(1, cols=False)), 1.0, 300.0, out, None) == E
+
+    # user-provided nodes
+    N = lib.RoxNodes(8, 1000)
+    args = (1, P, T, Q, 1.0, 18.0)
+    assert L.rox_xsec_nodes_batch(by(hit), by(lib.RoxNodes(None, 1000)), *args, 25.0, 0, 8, 256, 1 << 30, None) == E
+    assert L.rox_xsec_nodes_batch(by(hit), by(lib.RoxNodes(8, 0)), *args, 25.0, 0, 8, 256, 1 << 30, None) == E
+    assert L.rox_xsec_nodes_batch(by(hit), by(N), *args, 0.0, 0, 8, 256, 1 << 30, None) == E
+    assert L.rox_xsec_nodes_batch(by(hit), by(N), *args, 5000.0, 0, 8, 256, 1 << 30, None) == lib.ROX_ERANGE
+    assert L.rox_xsec_nodes_batch(by(hit), by(N), *args, 25.0, 0, 8, 256, 16, None) == lib.ROX_ENOMEM
