@@ -1,5 +1,9 @@
 """The C-ABI library loads without a GPU, exports every entry point declared in
-include/rox.h, and rejects invalid arguments on the host before any CUDA call."""
+include/rox.h, and rejects invalid arguments on the host before any CUDA call.
+
+The refusal tests pass placeholder device pointers that must never be dereferenced. They run
+only where no GPU is visible: there, a call that got past the host checks by mistake fails at
+its first CUDA call instead of launching on a bad address."""
 import ctypes
 import os
 import re
@@ -13,6 +17,17 @@ def _header_functions():
     src = open(os.path.join(ROOT, "include", "rox.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(rox_[a-z0-9_]+)\s*\(", src)))
+
+
+def _gpu_visible():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+host_only = pytest.mark.skipif(_gpu_visible(), reason="placeholder device pointers: runs only without a GPU")
 
 
 @pytest.fixture(scope="module")
@@ -32,6 +47,7 @@ def test_version(lib):
     assert "sm_103a" in lib.version()
 
 
+@host_only
 def test_invalid_arguments_rejected_on_host(lib):
     L = lib.lib
     G = lib.RoxGrid(2000.0, 0.01, 50001)
@@ -47,11 +63,9 @@ def test_invalid_arguments_rejected_on_host(lib):
     rc = L.rox_xsec(ctypes.byref(lines), ctypes.byref(big_grid), 1.0, 1000.0, 1.0, 1.0, 18.0, 25.0, 8, 256, 1 << 30,
                     None)
     assert rc == lib.ROX_ERANGE
-    for args in [(0.0, 1000.0, 1.0), (1.0, -5.0, 1.0), (1.0, 1000.0, 0.0), (-1.0, 1000.0, 1.0)]:
-        rc = L.rox_xsec(ctypes.byref(lines), ctypes.byref(G), args[0] if args[0] >= 0 else -1.0, args[1], args[2],
+    for args in [(1.0, -5.0, 1.0), (1.0, 1000.0, 0.0), (-1.0, 1000.0, 1.0)]:   # (P = 0 is valid)
+        rc = L.rox_xsec(ctypes.byref(lines), ctypes.byref(G), args[0], args[1], args[2],
                         1.0, 18.0, 25.0, 8, 256, 1 << 30, None)
-        if args == (0.0, 1000.0, 1.0):
-            continue  # P = 0 is valid (pure Doppler); reaching the launch needs a GPU
         assert rc == lib.ROX_EINVAL, args
     # ExoMol without g_up
     ex = lib.RoxLines(nu0=8, s_or_a=8, g_up=None, e_lower=8, gamma_ref=8, n_t=8, n=10, convention=1, width_dtype=0)
@@ -90,6 +104,7 @@ def test_static_scratch_holds_the_largest_static_problem():
     assert 0 < need <= 16 << 20, need
 
 
+@host_only
 def test_cia_arguments_rejected_on_host(lib):
     """CIA restructuring: every malformed layout is refused before anything reaches the GPU
     (the device pointers here are placeholders that are never dereferenced)."""
@@ -124,6 +139,7 @@ def test_cia_arguments_rejected_on_host(lib):
     assert call([300.0], [0, 4], [300.0], nodes=(None, 10)) == E         # nodes missing
 
 
+@host_only
 def test_extension_arguments_rejected_on_host(lib):
     """Selection, broadening descriptions and user-provided nodes: malformed arguments are
     refused on the host with the documented codes (device pointers are placeholders)."""
