@@ -91,7 +91,7 @@ __global__ void k_cia(const __grid_constant__ CiaArgs A, const double* __restric
               const long long mid = (lo + hi) >> 1;
               if (x[mid] > v) hi = mid; else lo = mid + 1;
             }
-            i = lo - 1;
+            i = min(max(lo - 1, 0LL), m - 2);   // lo in [1, m-1] for increasing samples
             xi = x[i]; xi1 = x[i + 1]; yi = y[i];
             dy = y[i + 1] - yi;
             r = 1.0 / (xi1 - xi);
@@ -219,7 +219,9 @@ k_cia_grid(const __grid_constant__ CiaArgs A, const CiaGrid g, const CiaTables T
           const long long step = (len + 31) >> 5;
           const long long off = (long long)lane * step;
           const bool le = off < len && c[lo + off] <= a;
-          const int k = __popc(__ballot_sync(0xffffffffu, le));   // probes 0 .. k-1 are <= a
+          // probes 0 .. k-1 are <= a; k >= 1 for increasing samples, and the clamp keeps every
+          // index inside the block for any data
+          const int k = max(1, __popc(__ballot_sync(0xffffffffu, le)));
           const long long nlo = lo + (long long)(k - 1) * step;
           len = min(step, lo + len - nlo);
           lo = nlo;

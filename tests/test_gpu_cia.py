@@ -156,3 +156,21 @@ def test_cia_grid_runs_and_edges():
         _same(got, ref, pts)
         on = np.isin(pts, x)                      # grid points on samples of the 500 K block: exact
         assert np.array_equal(got[1, on], ref[1, on])
+
+
+def test_cia_unsorted_samples_stay_in_bounds():
+    """Samples out of order break the documented precondition (the result is then unspecified),
+    but every index the kernels form stays inside its block: both paths run and write finite
+    values."""
+    rng = np.random.default_rng(4)
+    x = rng.uniform(100.0, 900.0, 500)                    # not sorted
+    y = rng.uniform(1.0, 2.0, 500)
+    nu, k = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    out = torch.empty((1, 20001), dtype=torch.float64, device="cuda")
+    _regrid([300.0], [0, 500], nu, k, (0.0, 0.05, 20001), [300.0], out)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    nodes = torch.from_numpy(np.linspace(0.0, 1000.0, 20001)).cuda()
+    rox.rox_cia_regrid_nodes([300.0], [0, 500], nu, k, nodes, [300.0], out)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
