@@ -43,6 +43,11 @@ cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes);
 cudaError_t rox_launch_select(const double* nu0, const double* S_T, long long n, int n_temps,
                               const unsigned long long* smax_bits, double origin, double width, long long n_bins,
                               double rel, int32_t* bin, unsigned long long* binmax_bits, float* S32, cudaStream_t s);
+cudaError_t rox_launch_select_reduced(const rox_lines* L, int n_temps, const double* temps, const double* q_of_temp,
+                                      double Q_ref, double* S_T, const unsigned long long* smax_bits, double origin,
+                                      double width, long long n_bins, double rel, int32_t* bin,
+                                      unsigned long long* binmax_fast, unsigned long long* binmax_exact, float* S32,
+                                      cudaStream_t s);
 cudaError_t rox_launch_broad_T(const RoxBroadDev& B, const float* a_coef, long long n, int n_temps,
                                const double* temps, float* G, float* gN, cudaStream_t s);
 cudaError_t rox_launch_lorentz_out(const RoxBroadDev& B, const float* a_coef, long long n, double P_bar, double T,
@@ -140,6 +145,7 @@ struct WsLayout {
   float2* span_base;
   int32_t* line_bin;   // main-contributor selection only: [n_lines] bins, [n_temps][n_bins] maxima,
   unsigned long long* binmax;
+  unsigned long long* binmax_exact;   // selection on reduced-form strengths: exact bin maxima
   uint8_t* keep_flags; //   per temperature the keep flags, the kept lines' indices and count, the span
   int32_t* keep_idx;   //   ranges over those indices, and the compaction's scratch
   long long* keep_count;
@@ -184,6 +190,7 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, b
   }
   w.line_bin = nullptr;
   w.binmax = nullptr;
+  w.binmax_exact = nullptr;
   w.keep_flags = nullptr;
   w.keep_idx = nullptr;
   w.keep_count = nullptr;
@@ -195,6 +202,8 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, b
     w.line_bin = (int32_t*)(base + off);
     off += rox_align256((size_t)(n_lines > 0 ? n_lines : 1) * 4);
     w.binmax = (unsigned long long*)(base + off);
+    off += rox_align256((size_t)n_temps * (size_t)n_bins * 8);
+    w.binmax_exact = (unsigned long long*)(base + off);
     off += rox_align256((size_t)n_temps * (size_t)n_bins * 8);
     const size_t nl = (size_t)(n_lines > 0 ? n_lines : 1);
     w.keep_flags = (uint8_t*)(base + off);
@@ -488,15 +497,14 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
                  : rox_launch_windows(lines->nu0, nl, grid, cutoff, nullptr, nullptr, nullptr, nullptr, w.geo,
                                       &w.hdr->evals_lines, &w.hdr->status, ROX_EUNSORTED, s);
     if ((rc = cuda_check(we, "windows kernel"))) return rc;
-    // a selection compares strengths against thresholds: there S(T) is the full FP64 form, so
-    // the kept set is decided on the same values as the definition's
     if ((rc = cuda_check(rox_launch_strengths_multi(lines, n_temps, temps.data(), qs.data(), Q_ref, w.S_T,
-                                                    w.hdr->smax_bits, sel != nullptr, s),
+                                                    w.hdr->smax_bits, false, s),
                          "strengths kernel")))
       return rc;
     const cudaError_t se =
-        sel ? rox_launch_select(lines->nu0, w.S_T, nl, n_temps, w.hdr->smax_bits, sel_origin, sel->bin_width, n_bins,
-                                sel->rel, w.line_bin, w.binmax, w.S32, s)
+        sel ? rox_launch_select_reduced(lines, n_temps, temps.data(), qs.data(), Q_ref, w.S_T, w.hdr->smax_bits,
+                                        sel_origin, sel->bin_width, n_bins, sel->rel, w.line_bin, w.binmax,
+                                        w.binmax_exact, w.S32, s)
             : rox_launch_scale_strengths(w.S_T, nl, n_temps, w.hdr->smax_bits, w.S32, s);
     if ((rc = cuda_check(se, "strength scaling kernel"))) return rc;
     if (sel) {

@@ -234,6 +234,59 @@ __global__ void k_bin_max(const int32_t* __restrict__ bin, const double* __restr
   }
 }
 
+// Selection on reduced-form strengths (relative error below 5e-7, see line_strength_fast):
+// every decision is taken as on the full FP64 strengths. A line whose reduced value is within
+// ROX_SEL_EPS of its bin's reduced maximum may hold the exact maximum: its FP64 strength
+// replaces the reduced one in S_T and the exact bin maxima are taken over those lines
+// (k_bin_max_fix). A line within ROX_SEL_EPS of its threshold rel * (exact maximum) is decided
+// on its FP64 strength; any other line lies on the same side of the threshold whichever form
+// is used (k_select_scale).
+#define ROX_SEL_EPS 1e-5
+__global__ void k_bin_max_fix(const rox_lines L, const __grid_constant__ TempSet ts, const int32_t* __restrict__ bin,
+                              double* S_T, long long n_bins, const unsigned long long* __restrict__ binmax_fast,
+                              unsigned long long* binmax_exact) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (int t = 0; t < ts.n; t++) {
+    double* S = S_T + (long long)t * L.n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) {
+      const int b = bin[i];
+      if (b < 0) continue;
+      const double mf = __longlong_as_double((long long)binmax_fast[(long long)t * n_bins + b]);
+      if (!(S[i] >= mf * (1.0 - ROX_SEL_EPS))) continue;
+      const double g = (L.convention == ROX_EXOMOL) ? (double)L.g_up[i] : 1.0;
+      const double sx = line_strength(ts.k[t], L.nu0[i], (double)L.s_or_a[i], g, (double)L.e_lower[i]);
+      S[i] = sx;
+      atomicMax(&binmax_exact[(long long)t * n_bins + b], (unsigned long long)__double_as_longlong(sx));
+    }
+  }
+}
+
+__global__ void k_select_scale(const rox_lines L, const __grid_constant__ TempSet ts, const double* __restrict__ S_T,
+                               const unsigned long long* __restrict__ smax_bits, const int32_t* __restrict__ bin,
+                               const unsigned long long* __restrict__ binmax_exact, long long n_bins, double rel,
+                               float* S32) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (int t = 0; t < ts.n; t++) {
+    const double smax = __longlong_as_double((long long)smax_bits[t]);
+    const double sc = ldexp(1.0, smax > 0.0 ? -ilogb(smax) : 0);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) {
+      double S = S_T[(long long)t * L.n + i];
+      const int b = bin[i];
+      bool keep = false;
+      if (b >= 0) {
+        const double thr =
+            __dmul_rn(rel, __longlong_as_double((long long)binmax_exact[(long long)t * n_bins + b]));
+        if (fabs(S - thr) <= ROX_SEL_EPS * thr) {   // near the threshold: the FP64 form decides
+          const double g = (L.convention == ROX_EXOMOL) ? (double)L.g_up[i] : 1.0;
+          S = line_strength(ts.k[t], L.nu0[i], (double)L.s_or_a[i], g, (double)L.e_lower[i]);
+        }
+        keep = S >= thr;
+      }
+      S32[(long long)t * L.n + i] = keep ? (float)(S * sc) : -0.0f;   // -0: dropped (+0: kept, below FP32)
+    }
+  }
+}
+
 // keep flags of the first temperature: the same test as k_scale_strengths
 __global__ void k_keep_flags(const double* __restrict__ S_T, const int32_t* __restrict__ bin,
                              const unsigned long long* __restrict__ binmax_bits, long long n, double rel,
@@ -360,6 +413,28 @@ cudaError_t rox_launch_select(const double* nu0, const double* S_T, long long n,
   k_line_bins<<<grid_for(n), 256, 0, s>>>(nu0, n, origin, width, n_bins, bin);
   k_bin_max<<<grid_for((n + ROX_BIN_RUN - 1) / ROX_BIN_RUN), 256, 0, s>>>(bin, S_T, n, n_temps, n_bins, binmax_bits);
   k_scale_strengths<<<grid_for(n), 256, 0, s>>>(S_T, n, n_temps, smax_bits, S32, bin, binmax_bits, n_bins, rel);
+  return cudaGetLastError();
+}
+
+// Selection for the cross-section launches, on strengths from k_strengths_multi<true> (the
+// reduced form): bins, reduced maxima, exact maxima over the candidate lines, then the
+// decisions and the scaled FP32 strengths (-0.0 for dropped lines).
+cudaError_t rox_launch_select_reduced(const rox_lines* L, int n_temps, const double* temps, const double* q_of_temp,
+                                      double Q_ref, double* S_T, const unsigned long long* smax_bits, double origin,
+                                      double width, long long n_bins, double rel, int32_t* bin,
+                                      unsigned long long* binmax_fast, unsigned long long* binmax_exact, float* S32,
+                                      cudaStream_t s) {
+  const long long n = L->n;
+  cudaError_t e = cudaMemsetAsync(binmax_fast, 0, (size_t)n_temps * (size_t)n_bins * 8, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(binmax_exact, 0, (size_t)n_temps * (size_t)n_bins * 8, s)) != cudaSuccess) return e;
+  TempSet ts;
+  ts.n = n_temps;
+  for (int t = 0; t < n_temps; t++) ts.k[t] = make_consts(L->convention, temps[t], q_of_temp[t], Q_ref);
+  k_line_bins<<<grid_for(n), 256, 0, s>>>(L->nu0, n, origin, width, n_bins, bin);
+  k_bin_max<<<grid_for((n + ROX_BIN_RUN - 1) / ROX_BIN_RUN), 256, 0, s>>>(bin, S_T, n, n_temps, n_bins, binmax_fast);
+  k_bin_max_fix<<<grid_for(n), 256, 0, s>>>(*L, ts, bin, S_T, n_bins, binmax_fast, binmax_exact);
+  k_select_scale<<<grid_for(n), 256, 0, s>>>(*L, ts, S_T, smax_bits, bin, binmax_exact, n_bins, rel, S32);
   return cudaGetLastError();
 }
 

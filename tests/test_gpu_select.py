@@ -87,9 +87,9 @@ def test_selected_cross_sections():
 
 def test_rel_zero_equals_unselected():
     """rel = 0 keeps every line that reaches the grid: the unselected result. The kept-line
-    index then lists every line the spans reach, in the same order; the selection takes S(T) in
-    the full FP64 form (it decides the kept set) and the plain launch in the reduced form, so
-    the two agree to a few 1e-7."""
+    index then lists every line the spans reach, in the same order; a few strengths the
+    selection recomputed in the FP64 form (bin maxima) differ from the plain launch's reduced
+    form by a few 1e-7, so the check allows rounding."""
     w = rs.CONFIGS[1]
     L = oracle.sort_lines(rs.make_lines(w))
     grid = rs.grid_of(w)
