@@ -574,10 +574,13 @@ def run_gpu(args):
                             "; two list buffers, step k+1's upload and sort overlap step k's cross-section"
                             if pipelined else "")},
                 "gpu_launches": args.steps * (6 if args.nodes or args.broadening else
-                                              7 if args.select is not None else 5),
-                "gpu_launches_note": "per step: %swindows, strengths, strength scaling, %stile ranges, Voigt "
-                                     "kernels (+ memsets)" % ("node offsets, " if args.nodes else "",
-                                                             "broadening, " if args.broadening else ""),
+                                              9 if args.select is not None else 5),
+                "gpu_launches_note": (
+                    "per step: windows, strengths, line bins, bin maxima, FP64 fix-up of the bin maxima, "
+                    "selection and scaling, kept flags, span ranges over the kept lines, Voigt kernel (+ CUB's "
+                    "two select kernels and memsets)" if args.select is not None else
+                    "per step: %swindows, strengths, strength scaling, %stile ranges, Voigt kernel "
+                    "(+ memsets)" % ("node offsets, " if args.nodes else "", "broadening, " if args.broadening else "")),
                 "clocks": csum}
         print(json.dumps(line))
     if dist is not None:
