@@ -1,9 +1,11 @@
 // a1 / a2: per-line strength S(T) and widths gamma_G, gamma_L.
 // pyROX paper, "Functionality of pyROX" -- "Compute line-strengths and -widths": the
 // strength and broadening widths of every transition at the user's pressure and
-// temperature. HBM-bound kernels: each thread reads one line's SoA entries (coalesced)
-// and writes its outputs; the Boltzmann and stimulated-emission factors and the partition
-// ratio are taken in FP64.
+// temperature. Each thread reads one line's SoA entries (coalesced) and writes its outputs.
+// The strength exists in two forms: the full FP64 one (line_strength), and for the
+// cross-section launches a reduced one (line_strength_fast) that keeps only the Boltzmann
+// exponent and its reduction in FP64. This GPU's FP64 rate, not the bytes, bounds these
+// kernels.
 #include <cuda_fp16.h>
 #include "rox_internal.cuh"
 
@@ -90,7 +92,8 @@ __global__ void k_widths(rox_lines L, double gG_fac, float l2_ratio, float p_fac
 }
 
 // S(T) for up to ROX_MAX_PT distinct temperatures in one launch, one sweep over the lines
-// per temperature (the FP64 exponentials, not the bytes, set its cost); the per-temperature maximum (needed to
+// per temperature (FAST: the reduced form; either way FP64 issue, not the bytes, sets its
+// cost); the per-temperature maximum (needed to
 // scale S into FP32 range inside the Voigt kernel) is reduced per warp and combined with
 // an atomic max on the (non-negative) double bit pattern, which is order-independent.
 struct TempSet {
