@@ -176,9 +176,11 @@ int rox_faddeeva_re(const float* x, const float* y, float* out, int64_t n, void*
  *           per call with a fixed summation order (bitwise reproducible run to run).
  * ws        device workspace of rox_xsec_workspace_size(lines->n, grid, n_temps) bytes, where
  *           n_temps is the number of distinct temperatures among T[0..n_pt-1] (S(T) is
- *           computed once per distinct temperature and kept in the workspace in FP64).
- * Voigt profile and tile sums in FP32 (compensated across line chunks); FP64 for the
- * Boltzmann / stimulated-emission factors, partition ratio and line-centre offsets. */
+ *           computed once per distinct temperature and kept in the workspace as a double).
+ * Voigt profile and tile sums in FP32 (compensated across line chunks). S(T): the Boltzmann
+ * exponent and its reduction k ln2 + r in FP64, exp(r), the stimulated-emission factor and the
+ * prefactor in FP32 (relative error below 1e-6, against 1e-16 for rox_line_strengths).
+ * Line-centre offsets: exact index decomposition in FP64. */
 size_t rox_xsec_workspace_size(int64_t n_lines, const rox_grid* grid, int n_temps);
 int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt,
                    const double* P_bar, const double* T, const double* Q_T, double Q_ref,
@@ -232,7 +234,10 @@ int rox_xsec_broadened_batch(const rox_lines* lines, const rox_grid* grid, const
 
 /* a4/a5 with main-contributor line selection (paper, "Compute line-strengths and -widths": the
  * line-profile step can be sped up by keeping only the main line-strength contributors).
- * At each (P,T) point, with S = S(T) in double precision, the lines are binned by nu0 into
+ * At each (P,T) point, with S = S(T) in double precision (as rox_line_strengths; the launch
+ * computes the reduced form of rox_xsec_batch and recomputes in double precision every line
+ * whose decision it could change, so every decision is the double-precision one), the lines
+ * are binned by nu0 into
  * bins of width bin_width (cm^-1) starting at grid->nu_min - cutoff,
  *   bin = floor((nu0 - (nu_min - cutoff)) / bin_width)   (subtraction and division each rounded
  *                                                         once in double precision),
@@ -365,7 +370,8 @@ typedef struct rox_job {
 } rox_job;
 
 /* a1 + a4 for many requests in one persistent launch (continuous-batching server, batched
- * windows): per job the strengths of its line range at its T (FP64, then scaled to FP32),
+ * windows): per job the strengths of its line range at its T (the reduced form of
+ * rox_xsec_batch, then scaled to FP32),
  * then one Voigt launch over all (job, span) items. Each job's result is independent of the
  * others in the launch (same summation order as alone). n_jobs <= ROX_MAX_PT,
  * n_lists <= 8. ws: rox_jobs_workspace_size(jobs, n_jobs) bytes. */
