@@ -444,7 +444,6 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   if (rc) return rc;
   RoxBroadDev bdev;
   if (br && (rc = check_broadening(br, lines, &bdev))) return rc;
-  if (rc) return rc;
   const bool on_nodes = nodes != nullptr;
   double sel_origin = 0.0;
   long long n_bins = 0;
