@@ -1,14 +1,17 @@
 #!/usr/bin/env python
 """Throughput of the line-by-line opacity cross-section hot path on GB300.
 
-Workload (default): the ExoMol-style single-(P,T) case -- 1e7 synthetic lines, nu0 uniform
-300-30000 cm^-1, grid 300-30000 cm^-1 at 0.01 cm^-1 (2,970,001 points), 25 cm^-1 wing
-cutoff, (P,T) = (0.1 bar, 1500 K). One step = one cross-section through the C ABI
-(rox_xsec) on the resident, nu0-sorted line list: line strengths and widths, windows and
-tile ranges, Voigt evaluation and accumulation. Metric: Voigt line-profile evaluations per
-second, one evaluation being a (line, grid point) pair inside the cutoff, counted exactly.
+Workload (default): the large-list case -- 1e9 synthetic HITRAN-style lines (half-precision
+widths, 20 B per line) held on the device as ten nu0-sorted chunks of 1e8, nu0 uniform
+500-10000 cm^-1, grid 500-10000 cm^-1 at 0.01 cm^-1 (950,001 points), 100 cm^-1 wing cutoff,
+(P,T) = (10 bar, 3000 K). One step = one cross-section of the whole list through the C ABI:
+rox_xsec_batch on each chunk in turn, the chunks after the first added into sigma
+(ROX_ACCUMULATE); each call computes strengths and widths, windows and span ranges, and runs the
+Voigt kernel. Metric: Voigt line-profile evaluations per second, one evaluation being a (line,
+grid point) pair inside the cutoff, counted exactly. (The 300-point batch case, 1e8 lines at
+15 P x 20 T, takes about a minute per step; it runs with --config 3.)
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rox|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rox|reference] [--config 1..4]
 
 --impl reference times the FP64 CPU oracle (scipy.special.wofz) on a bounded sample of
 the same workload on the host cores. Under torchrun (N > 1) every rank runs one replica
@@ -38,6 +41,9 @@ VOIGT_TRAFFIC_BYTES = 3.037e8
 # DRAM bytes of one k_cia_grid launch on the CIA workload (ncu dram__bytes_read + write,
 # profiles/k_cia_grid_40T_2970001pts.md; part of the 950 MB output is still in L2 at the end)
 CIA_TRAFFIC_BYTES = 9.086e8
+# DRAM bytes per evaluation of k_voigt on the large list (ncu dram__bytes_read + write on one
+# 1e7-line chunk of it, divided by that launch's evaluations); None until captured
+VOIGT_TRAFFIC_LARGE = None
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "Voigt line-profile evals/s"
@@ -50,7 +56,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rox", choices=["rox", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--chunk", type=int, default=100_000_000, help="lines per resident chunk (large list)")
+    ap.add_argument("--no-config2", action="store_true", help="skip the single-(P,T) exomol summary of the large run")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
@@ -70,8 +78,8 @@ def parse():
     ap.add_argument("--nodes", action="store_true",
                     help="user-provided grid: the workload's lines on nodes of fixed resolving power R = %g over the "
                          "same wavenumber range (rox_xsec_nodes_batch)" % rs.FIXED_R)
-    ap.add_argument("--serve-rates", default="50,100", help="Poisson request rates (req/s) of the serving leg")
-    ap.add_argument("--serve-seconds", type=float, default=6.0, help="arrival window per rate (s)")
+    ap.add_argument("--serve-rates", default="50,100,200,500", help="Poisson request rates (req/s) of the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window per rate (s)")
     return ap.parse_args()
 
 
@@ -163,25 +171,39 @@ def cpu_baseline(w, grid, P, T, q, Ls, target_s):
 def run_reference(args):
     """The reference arm: the FP64 oracle as it stands, on this host's cores (one spawned pool for
     the whole run), each step a bounded sample of random 256-point windows of the workload sized
-    to about 4 s of oracle work, so that per-task overheads do not dominate."""
+    to about 4 s of oracle work, so that per-task overheads do not dominate. Lists above 1e7 lines
+    are represented by their first 1e6 lines (the subsample the large list's accuracy is stated
+    on); workloads with several (P,T) points draw one per window."""
     import multiprocessing as mp
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w, grid, P, T, q = workload(args.config)
-    Ls = sorted_host_lines(w)
+    w = rs.CONFIGS[args.config]
+    grid = rs.grid_of(w)
+    q = rs.q_table(w)
+    Ls, n_sub = oracle_subsample(w)
     cores = len(os.sched_getaffinity(0))
-    Qt, Qr = q_oracle(q, T), q_oracle(q, 296.0)
+    Qr = q_oracle(q, 296.0)
+    pts = list(w.pts)
+    rng = np.random.default_rng(12)
+
+    def tasks_for(count, seed):
+        out = []
+        for k in range(count):
+            P, T = pts[int(rng.integers(0, len(pts)))]
+            out += oracle_sample_tasks(Ls, grid, P, T, q_oracle(q, T), Qr, w.mass_amu, w.cutoff, 1, 256, seed * 100003 + k)
+        return out
+
     total_ev, total_t = 0, 0.0
     with mp.get_context("spawn").Pool(cores) as pool:
-        probe = oracle_sample_tasks(Ls, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, cores, 256, 99)
+        probe = tasks_for(cores, 99)
         pool.map(_oracle_window, probe)                  # warm the workers (imports)
         t0 = time.perf_counter()
         pool.map(_oracle_window, probe, chunksize=1)
         per_window = (time.perf_counter() - t0) * cores / len(probe)   # core-seconds per window
         per_step = cores * max(2, int(round(4.0 / max(per_window, 1e-6))))
         for step in range(args.warmup + args.steps):
-            tasks = oracle_sample_tasks(Ls, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, per_step, 256, 100 + step)
+            tasks = tasks_for(per_step, 100 + step)
             t0 = time.perf_counter()
             res = pool.map(_oracle_window, tasks, chunksize=1)
             dt = time.perf_counter() - t0
@@ -189,24 +211,28 @@ def run_reference(args):
                 total_ev += sum(r[0] for r in res)
                 total_t += dt
     value = total_ev / total_t
+    lines_note = "all %d lines" % w.n_lines if n_sub == w.n_lines else "its first %d lines (of %d)" % (n_sub, w.n_lines)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "%s: %d lines, grid %d points, cutoff %g cm^-1, (P,T)=(%g bar, %g K)" % (
-                w.name, w.n_lines, grid[2], w.cutoff, P, T), "sample_per_step": "%d windows x 256 points" % per_step},
+            "config": {"workload": "%s: %d lines, grid %d points, cutoff %g cm^-1, %d (P,T) point(s)" % (
+                w.name, w.n_lines, grid[2], w.cutoff, len(pts)),
+                "sample_per_step": "%d windows x 256 points on %s" % (per_step, lines_note)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d steps of %d random 256-point windows (all lines within the cutoff of "
-                                       "each window), FP64 scipy.special.wofz, one pool of %d processes" % (
-                                           args.steps, per_step, cores)},
+                             "sample": "%d steps of %d random 256-point windows of the %s workload on %s (all of "
+                                       "them within the cutoff of each window), FP64 scipy.special.wofz, one pool "
+                                       "of %d processes" % (args.steps, per_step, w.name, lines_note, cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 # ------------------------------------------------------------------ serving leg (request latency)
-def serving_leg(rates, seconds):
+def serving_leg(rates, seconds, max_wait_s=2.0):
     """Four resident lists (1e5..1e8 lines, exomol distributions) on the 0.01 cm^-1 lattice of
-    300-30000 cm^-1; Poisson requests (list, P, T, window of 10-5000 cm^-1). Continuous batching
-    against the plain one-request-per-launch loop, same request stream."""
+    300-30000 cm^-1; Poisson requests (list, P, T, window of 10-5000 cm^-1) arriving for `seconds`
+    at each rate. Continuous batching against the plain one-request-per-launch loop, same request
+    stream, same number of launches in flight (3); requests queued longer than max_wait_s are
+    rejected (counted, not in the latency figures)."""
     import torch
     import paper_2510_20870_gb300 as rox
     from paper_2510_20870_gb300 import serve
@@ -222,25 +248,36 @@ def serving_leg(rates, seconds):
         del raw, ws
         lists.append(out)
     w0 = rs.SERVE_LISTS[0]
-    srv = serve.Server(lists, lattice, w0.cutoff, w0.mass_amu, rs.q_table(w0), max_inflight=3, max_batch=32)
+    srv = serve.Server(lists, lattice, w0.cutoff, w0.mass_amu, rs.q_table(w0), max_inflight=3, max_batch=32,
+                       max_wait_s=max_wait_s)
     srv.run(serve.requests_from_stream(rs.serve_requests(200.0, 16, seed=99), lattice), realtime=False)  # warm-up
     out = {}
     for rate in rates:
         reqs = serve.requests_from_stream(rs.serve_requests(rate, max(8, int(rate * seconds)), seed=5), lattice)
+        demand = sum(srv.work(r) for r in reqs) / max(r.t_arrival for r in reqs)
         legs = {}
         for name, opl in (("batched", False), ("one_per_launch", True)):
-            srv.evals, srv.launches = 0, 0
+            srv.evals, srv.launches, srv.max_queue_seen = 0, 0, 0
             t = time.perf_counter()
             res = srv.run(reqs, realtime=True, one_per_launch=opl)
             wall = time.perf_counter() - t
             st = serve.latency_stats(res)
-            st.update({"evals_per_s": srv.evals / wall, "launches": srv.launches, "wall_s": wall})
+            st.update({"served": len(res), "rejected": len(srv.rejected), "max_queued": srv.max_queue_seen,
+                       "evals_per_s": srv.evals / wall, "launches": srv.launches, "wall_s": wall})
             legs[name] = st
+        legs["requests"] = len(reqs)
+        legs["demand_evals_per_s"] = demand
         out["%g" % rate] = legs
+    budget = srv.mem_budget
     del srv, lists
     torch.cuda.empty_cache()
-    return {"workload": "4 resident lists (1e5, 1e6, 1e7, 1e8 lines), Poisson arrivals, list uniform, P log-uniform "
-                        "1e-5..1e2 bar, T uniform 300..3000 K, window 10..5000 cm^-1 at 0.01 cm^-1, cutoff 25",
+    return {"workload": "4 resident lists (1e5, 1e6, 1e7, 1e8 lines), Poisson arrivals for %g s per rate, list uniform, "
+                        "P log-uniform 1e-5..1e2 bar, T uniform 300..3000 K, window 10..5000 cm^-1 at 0.01 cm^-1, "
+                        "cutoff 25" % seconds,
+            "policy": "continuous batching: 3 launches in flight, shortest job first (requests waiting over 0.25 s "
+                      "first), at most 6e10 estimated evaluations per batch, device-memory budget %.1f GB (80%% of "
+                      "free memory), requests queued over %g s rejected; one_per_launch: one request per launch, "
+                      "3 in flight, same rejection rule" % (budget / 1e9, max_wait_s),
             "rates_req_per_s": out}
 
 
@@ -587,6 +624,318 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ roofline helpers
+def fp32_peaks(dev_index, sms):
+    """The Voigt kernel's roofline denominators: the formula peak (SMs x 128 FP32 lanes x 2 flop x
+    the maximum SM clock) and the FMA rate the probe kernel (include/rox.h rox_fp32_probe) sustains on
+    this GPU, timed with CUDA events while nvidia-smi samples the SM clock."""
+    import torch
+    from paper_2510_20870_gb300 import _binding as rb
+    nb = sms * 4
+    out = torch.empty(rb.rox_fp32_probe_out_size(nb) // 4, dtype=torch.float32, device="cuda")
+    rb.rox_fp32_probe(nb, 100, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev_index) as clk:
+        time.sleep(0.25)
+        e0.record()
+        fma = sum(rb.rox_fp32_probe(nb, 200_000, out) for _ in range(6))
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    c = clk.summary()
+    meas = 2.0 * fma / (ms * 1e-3) / 1e12
+    res = {"formula_tflops": sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12,
+           "formula_basis": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % (sms, SM_MAX_MHZ),
+           "measured_tflops": meas, "measured_ms": ms, "measured_sm_mhz": c.get("sm_mhz"),
+           "measured_basis": "rox_fp32_probe: %d blocks x 256 threads x 16 FMA chains, %.3g FMAs in %.1f ms "
+                             "(CUDA events)" % (nb, fma, ms)}
+    if c.get("sm_mhz"):
+        res["measured_fma_per_sm_clock"] = fma / (ms * 1e-3) / (sms * c["sm_mhz"] * 1e6)
+    return res
+
+
+def voigt_roofline(evals, kernel_ms, peaks, traffic, traffic_note, clocks):
+    achieved = evals * FLOPS_PER_EVAL / (kernel_ms * 1e-3) / 1e12
+    peak = peaks["formula_tflops"]
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "traffic_note": traffic_note, "kernel": "k_voigt", "kernel_ms": kernel_ms,
+            "peak_basis": peaks["formula_basis"], "flops_per_eval": FLOPS_PER_EVAL,
+            "peak_measured": peaks["measured_tflops"], "frac_of_measured": achieved / peaks["measured_tflops"],
+            "peak_measured_basis": peaks["measured_basis"], "peak_measured_sm_mhz": peaks.get("measured_sm_mhz")}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_median_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
+    return roof
+
+
+def oracle_subsample(w, n_sub=1_000_000):
+    """Host lines for the oracle legs: the whole list up to 1e7 lines, else its first n_sub lines
+    (generation indices 0..n_sub-1, regenerated on the host), sorted by nu0."""
+    import oracle
+    n = w.n_lines if w.n_lines <= 10_000_000 else n_sub
+    return oracle.sort_lines(rs.make_lines(w, 0, n)), n
+
+
+# ------------------------------------------------------------------ the large list (default workload)
+def run_large(args):
+    """Config 4: 1e9 lines held on the device as nu0-sorted chunks, one cross-section per step."""
+    import torch
+    import paper_2510_20870_gb300 as rox
+    from rox_synth.device import alloc_lines, make_lines_device
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    w = rs.CONFIGS[4]
+    grid = rs.grid_of(w)
+    (P, T), = w.pts
+    q = rs.q_table(w)
+    Qt, Qr = q_of(q, T), q_of(q, 296.0)
+    n = args.lines or w.n_lines
+    chunk = min(n, args.chunk)
+    starts = list(range(0, n, chunk))
+    cols = ["nu0", "s_or_a", "e_lower", "gamma_ref", "n_t"]
+    do_e2e = not args.no_e2e
+
+    # resident sorted chunks (the timed step's input) and, for the end-to-end leg, the unsorted
+    # chunks in pinned host memory
+    sort_ws = torch.empty(rox.rox_sort_workspace_size(chunk), dtype=torch.uint8, device=dev)
+    resident, host = [], []
+    for s0 in starts:
+        cnt = min(chunk, n - s0)
+        raw = make_lines_device(w, s0, cnt)
+        if do_e2e:
+            hp = {k: torch.empty(raw[k].shape, dtype=raw[k].dtype, pin_memory=True) for k in cols}
+            for k in cols:
+                hp[k].copy_(raw[k])
+            host.append(hp)
+        out = {k: torch.empty_like(raw[k]) for k in cols}
+        out["g_up"], out["convention"] = None, w.convention
+        rox.rox_sort_lines(raw, out, None, sort_ws)
+        resident.append(out)
+        del raw
+    torch.cuda.synchronize()
+    line_bytes = sum(v.numel() * v.element_size() for L in resident for k, v in L.items() if k in cols)
+    ws = torch.empty(rox.rox_xsec_workspace_size(chunk, grid, 1), dtype=torch.uint8, device=dev)
+    sigma = torch.empty((1, grid[2]), dtype=torch.float32, device=dev)
+
+    def step(evs=None, lines=resident, stream=None):
+        for c, L in enumerate(lines):
+            if evs is not None:
+                rox.rox_set_profile_events(*evs[c])
+            rox.rox_xsec_batch(L, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws,
+                               flags=rox.ROX_ACCUMULATE if c else 0, stream=stream)
+        if evs is not None:
+            rox.rox_set_profile_events(None, None)
+
+    # exact evaluation count of one step (the status call synchronises, so outside the timing)
+    evals = 0
+    for c, L in enumerate(resident):
+        rox.rox_xsec_batch(L, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws,
+                           flags=rox.ROX_ACCUMULATE if c else 0)
+        rc, ev = rox.rox_ws_status(ws)
+        if rc != 0:
+            raise RuntimeError(rox.lib.rox_last_error().decode())
+        evals += ev
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    ev_pairs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in starts]
+                for _ in range(args.steps)]
+    for pairs in ev_pairs:
+        for a, b in pairs:
+            a.record()
+            b.record()
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        time.sleep(0.3)
+        barrier()
+        t0.record()
+        for pairs in ev_pairs:
+            step(pairs)
+        t1.record()
+        barrier()
+    ms = t0.elapsed_time(t1)
+    voigt_ms = [sum(a.elapsed_time(b) for a, b in pairs) for pairs in ev_pairs]
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * evals * args.steps / (ms * 1e-3)
+    sig_max = float(sigma.max())
+    csum = clocks.summary()
+
+    # ---- end to end through the public API: every step uploads the unsorted chunks from pinned
+    # host memory (chunk c+1's upload and sort on a copy stream overlap chunk c's cross-section),
+    # sorts them (rox_sort_lines), adds each chunk's cross-section into sigma and reads sigma back
+    e2e = None
+    if do_e2e:
+        bufs = [alloc_lines(w, chunk, device=dev) for _ in range(2)]
+        sbufs = [{k: torch.empty_like(b[k]) for k in cols} for b in bufs]
+        for sb in sbufs:
+            sb["g_up"], sb["convention"] = None, w.convention
+        sort_b = [sort_ws, torch.empty_like(sort_ws)]
+        sigma_h = torch.empty((1, grid[2]), dtype=torch.float32, pin_memory=True)
+        main_s, copy_s = torch.cuda.current_stream(), torch.cuda.Stream()
+        up_ev = [torch.cuda.Event() for _ in range(2)]
+        comp_ev = [torch.cuda.Event() for _ in range(2)]
+        for b in range(2):
+            comp_ev[b].record(main_s)
+
+        def upload(c):
+            b = c % 2
+            cnt = min(chunk, n - starts[c])
+            copy_s.wait_event(comp_ev[b])
+            with torch.cuda.stream(copy_s):
+                raw = {k: bufs[b][k][:cnt] for k in cols}
+                for k in cols:
+                    raw[k].copy_(host[c][k], non_blocking=True)
+                raw["g_up"], raw["convention"] = None, w.convention
+                out = {k: sbufs[b][k][:cnt] for k in cols}
+                out["g_up"], out["convention"] = None, w.convention
+                rox.rox_sort_lines(raw, out, None, sort_b[b], stream=copy_s)
+            up_ev[b].record(copy_s)
+            return out
+
+        def e2e_step():
+            cur = upload(0)
+            for c in range(len(starts)):
+                nxt = upload(c + 1) if c + 1 < len(starts) else None
+                main_s.wait_event(up_ev[c % 2])
+                rox.rox_xsec_batch(cur, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws,
+                                   flags=rox.ROX_ACCUMULATE if c else 0)
+                comp_ev[c % 2].record(main_s)
+                cur = nxt
+            sigma_h.copy_(sigma, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        n_e2e = max(1, min(args.steps, 3))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main_s)
+        copy_s.wait_event(e0)
+        for _ in range(n_e2e):
+            e2e_step()
+        e1.record(main_s)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        if dist is not None:
+            tt = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        assert np.isfinite(sigma_h.numpy()).all()
+        h2d = sum(v.numel() * v.element_size() for hp in host for v in hp.values())
+        e2e = {"value": world * evals * n_e2e / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": sigma_h.numel() * 4, "ms_per_step": e2e_ms / n_e2e, "steps": n_e2e,
+               "includes": "per step: H2D of the %d unsorted chunks from pinned host memory, rox_sort_lines and "
+                           "rox_xsec_batch (ROX_ACCUMULATE) per chunk, D2H of sigma; chunk c+1's upload and sort "
+                           "overlap chunk c's cross-section" % len(starts)}
+        del bufs, sbufs, sort_b, host
+    del resident, ws, sort_ws
+    torch.cuda.empty_cache()
+
+    peaks = fp32_peaks(local, sms)
+    roof = voigt_roofline(evals, statistics.mean(voigt_ms), peaks,
+                          VOIGT_TRAFFIC_LARGE * evals if VOIGT_TRAFFIC_LARGE else None,
+                          "ncu dram__bytes_read + write of k_voigt on one 1e7-line chunk of this workload, per "
+                          "evaluation, times this step's evaluations (the kernel reads each line once per span it "
+                          "reaches; the traffic grows with the evaluations)", csum)
+    roof["kernel_ms_note"] = "sum over the %d chunk launches of one step (CUDA events around each launch)" % len(starts)
+
+    extra2 = None
+    if rank == 0 and world == 1 and not args.no_config2:
+        extra2 = config2_summary(args, peaks)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serving = serving_leg([float(r) for r in args.serve_rates.split(",")], args.serve_seconds)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Ls, n_sub = oracle_subsample(w)
+        cpu = cpu_baseline(w, grid, P, T, q, Ls, args.cpu_seconds)
+        cpu["sample"] = "lines 0..%d of the large list (its 1e6-line subsample, all of them within the cutoff of " \
+                        "each window); " % (n_sub - 1) + cpu["sample"]
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "large: %d HITRAN-style lines (f16 widths, 20 B per line) as %d device-resident "
+                                       "nu0-sorted chunks, grid %g-%g cm^-1 at %g (%d points), cutoff %g cm^-1, "
+                                       "(P,T)=(%g bar, %g K)" % (n, len(starts), w.grid_lo, w.grid_hi, w.dnu, grid[2],
+                                                                 w.cutoff, P, T),
+                           "evals_per_step": evals, "xsecs_per_s": world * args.steps / (ms * 1e-3),
+                           "step": "rox_xsec_batch per chunk (strengths, widths, windows, span ranges, Voigt "
+                                   "accumulate), chunks after the first with ROX_ACCUMULATE",
+                           "l2": "inputs larger than L2 (line list %.1f GB)" % (line_bytes / 1e9),
+                           "sigma_max": sig_max, "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "config2": extra2, "serving": serving,
+                "gpu_launches": args.steps * 5 * len(starts),
+                "gpu_launches_note": "per chunk: windows, strengths, strength scaling, span ranges, Voigt kernel "
+                                     "(+ memsets)",
+                "clocks": csum}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def config2_summary(args, peaks):
+    """The single-(P,T) exomol workload (1e7 lines, 2,970,001 points), timed like the main run, as a
+    second figure beside the large list."""
+    import torch
+    import paper_2510_20870_gb300 as rox
+    from rox_synth.device import make_lines_device
+    w, grid, P, T, q = workload(2)
+    Qt, Qr = q_of(q, T), q_of(q, 296.0)
+    raw = make_lines_device(w, 0, w.n_lines)
+    lines = {k: (torch.empty_like(v) if isinstance(v, torch.Tensor) else v) for k, v in raw.items()}
+    sws = torch.empty(rox.rox_sort_workspace_size(w.n_lines), dtype=torch.uint8, device="cuda")
+    rox.rox_sort_lines(raw, lines, None, sws)
+    del raw, sws
+    ws = torch.empty(rox.rox_xsec_workspace_size(w.n_lines, grid, 1), dtype=torch.uint8, device="cuda")
+    sigma = torch.empty((1, grid[2]), dtype=torch.float32, device="cuda")
+    rox.rox_xsec(lines, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
+    rc, evals = rox.rox_ws_status(ws)
+    for _ in range(args.warmup):
+        rox.rox_xsec(lines, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
+    steps = max(args.steps, 10)
+    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in pairs:
+        a.record()
+        b.record()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for a, b in pairs:
+        rox.rox_set_profile_events(a, b)
+        rox.rox_xsec(lines, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
+    rox.rox_set_profile_events(None, None)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    kms = statistics.mean(a.elapsed_time(b) for a, b in pairs)
+    del lines, ws, sigma
+    torch.cuda.empty_cache()
+    return {"workload": "exomol: %d lines, grid %d points, cutoff %g cm^-1, (P,T)=(%g bar, %g K)" % (
+                w.n_lines, grid[2], w.cutoff, P, T),
+            "value": evals / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "status": rc,
+            "kernel_ms": kms, "xsecs_per_s": 1e3 / ms,
+            "roofline_frac": evals * FLOPS_PER_EVAL / (kms * 1e-3) / 1e12 / peaks["formula_tflops"]}
+
+
 # ------------------------------------------------------------------ other workloads (documentation runs)
 def _sorted_device_lines(w, start, count, stream=None):
     import torch
@@ -640,69 +989,6 @@ def run_batch_config(args):
                                              "points, cutoff %g" % (n, len(pts), grid[2], w.cutoff),
                                  "evals_per_step": evals, "xsecs_per_s": len(pts) / (ms * 1e-3)},
                       "clocks": clocks.summary(), "status": rc}))
-
-
-def run_stream_config(args):
-    """Config 4: 1e9 lines in device-resident chunks (generated and sorted on the device), the
-    next chunk prepared on a second stream while the current one is evaluated, all chunks added
-    into one sigma."""
-    import torch
-    import paper_2510_20870_gb300 as rox
-    w = rs.CONFIGS[4]
-    grid = rs.grid_of(w)
-    (P, T), = w.pts
-    q = rs.q_table(w)
-    Qt, Qr = q_of(q, T), q_of(q, 296.0)
-    n = args.lines or w.n_lines
-    chunk = min(n, 100_000_000)
-    n_chunks = (n + chunk - 1) // chunk
-    sigma = torch.zeros((1, grid[2]), dtype=torch.float32, device="cuda")
-    ws = torch.empty(rox.rox_xsec_workspace_size(chunk, grid, 1), dtype=torch.uint8, device="cuda")
-    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
-
-    def step():
-        sigma.zero_()
-        total = 0
-        ready = torch.cuda.Event()
-        with torch.cuda.stream(side):
-            nxt, keep = _sorted_device_lines(w, 0, min(chunk, n), stream=side)
-            ready.record(side)
-        for c in range(n_chunks):
-            cur, cur_keep = nxt, keep
-            main.wait_event(ready)
-            if c + 1 < n_chunks:
-                ready = torch.cuda.Event()
-                with torch.cuda.stream(side):
-                    side.wait_stream(main)
-                    s0 = (c + 1) * chunk
-                    nxt, keep = _sorted_device_lines(w, s0, min(chunk, n - s0), stream=side)
-                    ready.record(side)
-            rox.rox_xsec_batch(cur, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws,
-                               flags=rox.ROX_ACCUMULATE)
-            rc, ev = rox.rox_ws_status(ws)
-            total += ev
-            del cur, cur_keep
-        return total
-    step()
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    with ClockSampler(0) as clocks:
-        for _ in range(args.steps):
-            evals = step()
-        torch.cuda.synchronize()
-    ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    sig = sigma.cpu().numpy()
-    print(json.dumps({"metric": METRIC, "value": evals / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-                      "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                      "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": "large: %d lines in %d device-resident chunks (generated and sorted on the "
-                                             "device, next chunk on a second stream), grid %d points, cutoff %g" % (
-                                                 n, n_chunks, grid[2], w.cutoff),
-                                 "evals_per_step": evals, "timing": "host wall clock around the chunk loop",
-                                 "sigma_finite": bool(np.isfinite(sig).all()), "sigma_max": float(sig.max())},
-                      "clocks": clocks.summary()}))
 
 
 def run_cia(args):
@@ -797,7 +1083,7 @@ def main():
     elif args.config == 3:
         run_batch_config(args)
     elif args.config == 4:
-        run_stream_config(args)
+        run_large(args)
     else:
         run_gpu(args)
 

@@ -385,6 +385,16 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
  * stream. Pass NULL, NULL to stop. Recording is stream-ordered and adds no sync. */
 int rox_set_profile_events(void* start, void* stop);
 
+/* Measurement helper (the paper has no counterpart): the FP32 fused multiply-add rate of this
+ * GPU, the denominator of the Voigt kernel's roofline. Launches n_blocks blocks of 256 threads,
+ * each thread running 16 independent FMA chains for reps x 8 rounds; out is a DEVICE buffer of
+ * at least rox_fp32_probe_out_size(n_blocks) bytes (caller-owned, overwritten with values of no
+ * use). *fma_out (host) receives the number of FMAs the launch performs; time the launch with
+ * events on `stream` and divide. ROX_EINVAL for n_blocks < 1, reps < 1 or NULL pointers,
+ * ROX_ENOMEM for a short buffer. */
+size_t rox_fp32_probe_out_size(int n_blocks);
+int rox_fp32_probe(int n_blocks, int reps, float* out, size_t out_bytes, double* fma_out, void* stream);
+
 /* Allocation-free variant of rox_xsec (one (P,T) point), for callers that cannot
  * allocate device memory themselves: an application whose own memory manager owns all
  * device memory, a plugin that is not allowed to call cudaMalloc, or an interface that

@@ -116,6 +116,8 @@ def _load():
         "rox_cia_regrid": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P, ctypes.c_size_t, P]),
         "rox_cia_regrid_nodes": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P]),
         "rox_xsec_broadened_workspace_size": (ctypes.c_size_t, [I64, P, ctypes.c_int]),
+        "rox_fp32_probe_out_size": (ctypes.c_size_t, [ctypes.c_int]),
+        "rox_fp32_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P, P]),
         "rox_xsec_broadened_batch": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P,
                                                     ctypes.c_size_t, P]),
     }
@@ -436,6 +438,18 @@ def rox_xsec_jobs(prepared_lists, jobs, ws, stream=None):
     lists = (RoxPrepared * len(prepared_lists))(*[p.struct for p in prepared_lists])
     arr = (RoxJob * len(jobs))(*jobs)
     _check(lib.rox_xsec_jobs(lists, len(prepared_lists), arr, len(jobs), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def rox_fp32_probe(n_blocks, reps, out, stream=None):
+    """Launch the FP32 FMA-rate probe (include/rox.h); returns the number of FMAs it performs."""
+    fma = ctypes.c_double(0.0)
+    _check(lib.rox_fp32_probe(int(n_blocks), int(reps), _ptr(out), out.numel() * out.element_size(),
+                              ctypes.byref(fma), _stream(stream)))
+    return fma.value
+
+
+def rox_fp32_probe_out_size(n_blocks):
+    return int(lib.rox_fp32_probe_out_size(int(n_blocks)))
 
 
 def rox_ws_status(ws, stream=None):

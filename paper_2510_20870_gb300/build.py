@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librox.so")
 HOST_LIB = os.path.join(HERE, "librox_fadd_host.so")
-SOURCES = ["rox_api.cu", "rox_params.cu", "rox_geometry.cu", "rox_voigt.cu", "rox_static.cu", "rox_cia.cu"]
+SOURCES = ["rox_api.cu", "rox_params.cu", "rox_geometry.cu", "rox_voigt.cu", "rox_static.cu", "rox_cia.cu", "rox_probe.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

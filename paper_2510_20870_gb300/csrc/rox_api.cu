@@ -543,7 +543,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   L0.nu_min_f = on_nodes ? 0.0f : (float)grid->nu_min;
   L0.width_f16 = lines->width_dtype == ROX_WIDTH_F16;
   L0.idx = nullptr;
-  L0.pad = 0;
+  L0.inv_dnu_f = on_nodes ? 0.0f : (float)(1.0 / grid->dnu);
   std::vector<RoxJobDev> jobs(n_pt);
   for (int k = 0; k < n_pt; k++) {
     RoxJobDev& J = jobs[k];
@@ -912,7 +912,7 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     L[l].dnu_f = (float)P.lattice.dnu;
     L[l].nu_min_f = (float)P.lattice.nu_min;
     L[l].width_f16 = P.lines.width_dtype == ROX_WIDTH_F16;
-    L[l].pad = 0;
+    L[l].inv_dnu_f = (float)(1.0 / P.lattice.dnu);
   }
   std::vector<RoxJobDev> J(n_jobs);
   for (int k = 0; k < n_jobs; k++) {

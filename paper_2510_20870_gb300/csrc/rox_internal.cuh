@@ -72,7 +72,7 @@ struct RoxListDev {
   float dnu_f;
   float nu_min_f;
   int32_t width_f16;
-  int32_t pad;
+  float inv_dnu_f;            // 1/dnu (uniform grid; 0 on nodes)
 };
 
 // Lorentz-width description of rox_broadening in kernel parameter form

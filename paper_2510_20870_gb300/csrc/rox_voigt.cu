@@ -18,15 +18,15 @@
 // S V = (S Y / pi)(t + K) / (t^2 + B) with t = X^2 + A, A = alpha gamma_G^2,
 // B = beta gamma_G^4, K = kappa gamma_G^2, i.e. 4 FMAs and one reciprocal; two lines share
 // one reciprocal (n1/d1 + n2/d2 = (n1 d2 + n2 d1)/(d1 d2)), so a pair costs 12 FP32
-// operations and one MUFU per point. The slow zone is x^2 + y^2 < 6.5^2 for y < 0.5 (per-line
-// Pade form) and < 22^2 otherwise (2-level continued fraction), at least the precision margin.
-// Lines are evaluated in two passes per batch. Pass 1 applies the far formula to every line
-// whose window covers the span, in pairs, with the numerator set to zero inside the line's
-// slow zone (t < t_z, one precomputed threshold); lines cut by a window edge take the same
-// masked formula in pairs too, with per-point window masks. Pass 2 evaluates exactly the
-// complementary points (t < t_z, decided on the same rounded t) with the full FP32 Faddeeva
-// forms (rox_faddeeva.cuh), one form per 32-point sub-span where possible, accumulated in
-// warp-private shared memory.
+// operations and one MUFU per point, three of them as paired (f32x2) instructions. The slow
+// zone is x^2 + y^2 < 6.5^2 for y < 0.5 (per-line Pade form) and < 22^2 otherwise (2-level
+// continued fraction), at least the precision margin.
+// Lines are evaluated in two passes per batch. Pass 1 applies the far formula to every line at
+// every point of its window, in pairs; a line whose slow zone meets the span has t clamped to
+// the zone boundary, t = max(t, t_z), so inside the zone it adds the far form's (finite) value
+// at the boundary. Pass 2 visits exactly those points (t < t_z, decided on the same rounded t)
+// and adds the full FP32 Faddeeva forms (rox_faddeeva.cuh) minus that boundary value, one form
+// per 32-point sub-span where possible, accumulated in warp-private shared memory.
 #include <cuda_fp16.h>
 #include "rox_internal.cuh"
 #include "rox_faddeeva.cuh"
@@ -36,17 +36,31 @@ namespace {
 #define ROX_NDAW (ROX_DAW_NODES * ROX_DAW_STRIDE)
 #define ROX_INV_PI 0.318309886183790672f
 
-// Per-line constants of one (P,T) point, one record per staged line:
-//   a = {k0 (exact float), f*dnu, A, B}            (far form t = X^2 + A, d = t^2 + B)
-//   b = {S Y / pi, (S Y / pi) K, class bits (1: window covers the span, 2: slow zone meets
-//        the span), t_z (far formula iff t >= t_z)}
-//   c = {jlo, jhi, zlo, zhi} (int bits; window and slow zone, inclusive grid indices)
-//   d = {1/gamma_G, y = gamma_L/gamma_G, S/(gamma_G sqrt(pi)), 1 if the slow zone is |z| < 6.5
-//        (per-line Pade far form, not widened by the precision margin), else 0}
-// S is scaled by 2^-e (e the exponent of the largest strength at this temperature).
-struct __align__(16) Rec {
-  float4 a, b, c, d;
+// Per-line constants of one (P,T) point for the batch in hand. Each line has a slot; slots are
+// ordered by class -- lines whose window covers the whole span and whose slow zone misses it
+// ("clean") first, then the other covering lines, then the lines cut by a window edge -- and
+// slots 2k, 2k+1 form pair k. The pair tables hold both lines' far-form constants side by side,
+// so one 16-byte load brings a field of both; the line table holds what window edges and pass 2
+// need per slot. S is scaled by 2^-e (e the exponent of the largest strength at this
+// temperature).
+struct PairTab {
+  float4 ab[16];   // {A0, A1, B0, B1}: far form t = X^2 + A, d = t^2 + B
+  float4 pq[16];   // {P0, P1, Q0, Q1}: S V = (P t + Q) / d, P = S Y / pi, Q = P K
+  float4 ef[16];   // uniform grid {E0, E1, F0, F1}: X at the lane's first point = (lane + E) dnu + F,
+                   // E = (span start) - k0 (exact), F = -f dnu; nodes {ch0, ch1, cl0, cl1}: X = (D.hi - ch) + (D.lo - cl)
+  float2 tz[16];   // {t_z0, t_z1}: the far form holds for t >= t_z; pass 1 evaluates it at max(t, t_z)
 };
+struct LineTab {
+  int2 W[32];      // window [jlo, jhi] (grid indices)
+  int2 Z[32];      // slow zone [zlo, zhi] (grid indices; nodes: the window)
+  float iG[32];    // 1/gamma_G; negative if the slow zone is |z| < 6.5 not widened by the margin
+  float y[32];     // gamma_L / gamma_G
+  float pc[32];    // S / (gamma_G sqrt(pi))
+  float cf[32];    // the far form at t = t_z, which pass 1 adds at every point of the slow zone
+};
+// one line's field out of a pair table row: half h (0, 1) of {lo, hi} pairs
+__device__ __forceinline__ float row_lo(const float4& v, int h) { return h ? v.y : v.x; }
+__device__ __forceinline__ float row_hi(const float4& v, int h) { return h ? v.w : v.z; }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -79,95 +93,171 @@ __device__ __forceinline__ void load_widths(const RoxJobDev& J, const RoxListDev
   }
 }
 
-// one point of one line outside the slow zone: S V = n / d
-__device__ __forceinline__ float far_term(float X, const float4& a, const float4& b) {
-  float t = fmaf(X, X, a.z);
-  float d = fmaf(t, t, a.w);
-  float n = fmaf(t, b.x, b.y);
-  return n * rox_rcp(d);
+// Two FP32 values in one 64-bit register pair, for the paired FP32 instructions of sm_100 and
+// later (fma.rn.f32x2 / add.rn.f32x2: two IEEE operations, each rounded as the scalar one). A
+// paired instruction takes one issue slot for two operations, which leaves issue slots to the
+// reciprocal, the clamps and the loads while the FMA pipes stay busy.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
 }
 
-// far formula with the slow-zone mask of pass 1: zero where t < t_z (there the denominator,
-// which may vanish inside the zone, is replaced by 1)
-__device__ __forceinline__ float masked_far(float X, const float4& a, const float4& b) {
-  const float t = fmaf(X, X, a.z);
-  const bool f = t >= b.w;
-  const float d = f ? fmaf(t, t, a.w) : 1.0f;
-  const float n = f ? fmaf(t, b.x, b.y) : 0.0f;
-  return n * rox_rcp(d);
+// Far-form constants of pair k, packed for the paired instructions.
+struct PairC {
+  f32x2 A, B, P, Q;
+  float2 T;
+  float e0, e1, f0, f1;
+};
+template <bool CLAMP>
+__device__ __forceinline__ PairC pair_consts(const PairTab& P, int k) {
+  PairC c;
+  const float4 ab = P.ab[k], pq = P.pq[k], ef = P.ef[k];
+  c.A = f2_pack(ab.x, ab.y);
+  c.B = f2_pack(ab.z, ab.w);
+  c.P = f2_pack(pq.x, pq.y);
+  c.Q = f2_pack(pq.z, pq.w);
+  c.T = CLAMP ? P.tz[k] : make_float2(0.0f, 0.0f);
+  c.e0 = ef.x;
+  c.e1 = ef.y;
+  c.f0 = ef.z;
+  c.f1 = ef.w;
+  return c;
 }
 
-// X = nu - nu0 at this lane's point of sub-span m. Uniform grid: X0 + 32 m dnu, X0 the offset
-// at the lane's first point (from the exact index decomposition). User-provided nodes: the
-// node's double-float offset from the span's first node, D[32 m] = {hi, lo}, minus the line's,
-// a = {c hi, c lo}; the hi parts cancel exactly near the line, so X keeps its relative accuracy.
+// acc + S0 V0 + S1 V1 for the pair's offsets x0, x1 at one point, the two fractions over one
+// reciprocal, n0/d0 + n1/d1 = (n0 d1 + n1 d0)/(d0 d1). CLAMP: t = max(X^2 + A, t_z) per line
+// (inside its slow zone a line contributes the far form's value at the zone boundary, which
+// pass 2 takes out again). MASK: u0, u1 tell whether the point is in each line's window.
+// Paired: X^2 + A, t^2 + B, P t + Q; scalar: 4 FP32 operations and 1 MUFU (+ 2 clamps).
+template <bool CLAMP, bool MASK>
+__device__ __forceinline__ float pair_add(float x0, float x1, const PairC& c, bool u0, bool u1, float acc) {
+  const f32x2 x = f2_pack(x0, x1);
+  f32x2 t = f2_fma(x, x, c.A);
+  if (CLAMP) {
+    float t0, t1;
+    f2_unpack(t, t0, t1);
+    t = f2_pack(fmaxf(t0, c.T.x), fmaxf(t1, c.T.y));
+  }
+  float d0, d1, n0, n1;
+  f2_unpack(f2_fma(t, t, c.B), d0, d1);
+  f2_unpack(f2_fma(t, c.P, c.Q), n0, n1);
+  if (MASK) {
+    n0 = u0 ? n0 : 0.0f;
+    n1 = u1 ? n1 : 0.0f;
+  }
+  return fmaf(fmaf(n1, d0, n0 * d1), rox_rcp(d0 * d1), acc);
+}
+
+// The pair's offsets at this lane's first point (uniform grid): X = (lane + E) dnu + F, with
+// lane + E = (span start + lane) - k0 exact, so X is the exact index decomposition rounded once.
 template <bool NU>
-__device__ __forceinline__ float pos(int m, float X0, const float4& a, const float2* D, float dnu_f) {
+__device__ __forceinline__ void pair_x0(const PairC& c, float lanef, float dnu_f, float& X0, float& X1) {
+  if constexpr (NU) {
+    X0 = X1 = 0.0f;
+  } else {
+    f2_unpack(f2_fma(f2_add(f2_pack(lanef, lanef), f2_pack(c.e0, c.e1)), f2_pack(dnu_f, dnu_f), f2_pack(c.f0, c.f1)),
+              X0, X1);
+  }
+}
+
+// X = nu - nu0 at this lane's point of sub-span m. Uniform grid: X0 + 32 m dnu (one rounding more).
+// User-provided nodes: the node's double-float offset from the span's first node, D[32 m] =
+// {hi, lo}, minus the line's {ch, cl}; the hi parts cancel exactly near the line, so X keeps
+// its relative accuracy.
+template <bool NU>
+__device__ __forceinline__ float pos(int m, float X0, float ch, float cl, const float2* D, float dnu_f) {
   if constexpr (NU) {
     const float2 d = D[32 * m];
-    return (d.x - a.x) + (d.y - a.y);
+    return (d.x - ch) + (d.y - cl);
   } else {
     return fmaf((float)(32 * m), dnu_f, X0);
   }
 }
 
-// Pass 1 for a line whose window edge falls inside the span: per 32-point sub-span, skipped if
-// outside the window, the masked far formula otherwise, masked per point where cut.
-template <bool NU>
-__device__ __forceinline__ void edge_line(const float4& a, const float4& b, const float4& c, int Aw, int lane,
-                                          float Jf, float dnu_f, const float2* D, float (&acc)[ROX_K]) {
-  const float X0 = fmaf(Jf - a.x, dnu_f, -a.y);
-  const int jlo = __float_as_int(c.x), jhi = __float_as_int(c.y);
+// Pass 1 for covering pair k: every point of the span (CLAMP unless both lines are clean).
+template <bool NU, bool CLAMP>
+__device__ __forceinline__ void cover_pair(const PairTab& P, int k, float lanef, float dnu_f, const float2* D,
+                                           float (&acc)[ROX_K]) {
+  const PairC c = pair_consts<CLAMP>(P, k);
+  float X0, X1;
+  pair_x0<NU>(c, lanef, dnu_f, X0, X1);
 #pragma unroll
-  for (int m = 0; m < ROX_K; m++) {
-    const int am = Aw + 32 * m, bm = am + 31;
-    if (bm < jlo || am > jhi) continue;
-    const int j = am + lane;
-    const float v = masked_far(pos<NU>(m, X0, a, D, dnu_f), a, b);
-    acc[m] += (j >= jlo && j <= jhi) ? v : 0.0f;
-  }
+  for (int m = 0; m < ROX_K; m++)
+    acc[m] = pair_add<CLAMP, false>(pos<NU>(m, X0, c.e0, c.f0, D, dnu_f), pos<NU>(m, X1, c.e1, c.f1, D, dnu_f), c,
+                                    true, true, acc[m]);
 }
 
-// Pass 1 for two lines cut by window edges, sharing one reciprocal as the covering lines do.
-// The sub-spans outside both windows are skipped (warp-uniform test); elsewhere each point
-// takes line i iff it lies in the window, m in [ceil((jlo-Aw-lane)/32), floor((jhi-Aw-lane)/32)]
-// (the exact integer window), and outside the slow zone. Lines arrive sorted by nu0, so
-// paired edge lines have their edges in the same or a neighbouring sub-span.
+// Pass 1 for pair k of which at least one line is cut by a window edge: the sub-spans outside
+// both windows are skipped (warp-uniform test); the sub-spans inside both windows take every
+// point; elsewhere each point takes line i iff it lies in the line's window, m in
+// [ceil((jlo-Aw-lane)/32), floor((jhi-Aw-lane)/32)] (the exact integer window). Lines arrive
+// sorted by nu0, so paired edge lines have their edges in the same or a neighbouring sub-span.
 template <bool NU>
-__device__ __forceinline__ void edge_pair(const Rec& r0, const Rec& r1, int Aw, int lane, float Jf, float dnu_f,
-                                          const float2* D, float (&acc)[ROX_K]) {
-  const float4 a0 = r0.a, b0 = r0.b, a1 = r1.a, b1 = r1.b;
-  const int lo0 = __float_as_int(r0.c.x) - Aw, hi0 = __float_as_int(r0.c.y) - Aw;
-  const int lo1 = __float_as_int(r1.c.x) - Aw, hi1 = __float_as_int(r1.c.y) - Aw;
+__device__ __forceinline__ void edge_pair(const PairTab& P, const LineTab& L, int k, int Aw, int lane, float lanef,
+                                          float dnu_f, const float2* D, float (&acc)[ROX_K]) {
+  const PairC c = pair_consts<true>(P, k);
+  const int2 w0 = L.W[2 * k], w1 = L.W[2 * k + 1];
+  const int lo0 = w0.x - Aw, hi0 = w0.y - Aw, lo1 = w1.x - Aw, hi1 = w1.y - Aw;
   const int mf = max(0, min(lo0, lo1) >> 5), ml = min(ROX_K - 1, max(hi0, hi1) >> 5);
   const int mlo0 = (lo0 - lane + 31) >> 5, mhi0 = (hi0 - lane) >> 5;   // this lane's window, in m
   const int mlo1 = (lo1 - lane + 31) >> 5, mhi1 = (hi1 - lane) >> 5;
-  // sub-spans inside both windows, when neither line's slow zone meets the span: no masks
-  const bool nozone = !((__float_as_uint(b0.z) | __float_as_uint(b1.z)) & 2u);
-  const int cf = nozone ? max((lo0 + 31) >> 5, (lo1 + 31) >> 5) : ROX_K;
-  const int cl = min((hi0 - 31) >> 5, (hi1 - 31) >> 5);
-  const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y), X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
+  const int cf = max((lo0 + 31) >> 5, (lo1 + 31) >> 5), cl = min((hi0 - 31) >> 5, (hi1 - 31) >> 5);
+  float X0, X1;
+  pair_x0<NU>(c, lanef, dnu_f, X0, X1);
 #pragma unroll
   for (int m = 0; m < ROX_K; m++) {
     if (m < mf || m > ml) continue;
-    const float x0 = pos<NU>(m, X0, a0, D, dnu_f), x1 = pos<NU>(m, X1, a1, D, dnu_f);
-    const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
+    const float x0 = pos<NU>(m, X0, c.e0, c.f0, D, dnu_f), x1 = pos<NU>(m, X1, c.e1, c.f1, D, dnu_f);
     if (m >= cf && m <= cl) {
-      const float d0 = fmaf(t0, t0, a0.w), d1 = fmaf(t1, t1, a1.w);
-      const float n0 = fmaf(t0, b0.x, b0.y), n1 = fmaf(t1, b1.x, b1.y);
-      acc[m] = fmaf(fmaf(n1, d0, n0 * d1), rox_rcp(d0 * d1), acc[m]);
-      continue;
+      acc[m] = pair_add<true, false>(x0, x1, c, true, true, acc[m]);
+    } else {
+      acc[m] = pair_add<true, true>(x0, x1, c, m >= mlo0 && m <= mhi0, m >= mlo1 && m <= mhi1, acc[m]);
     }
-    const bool f0 = t0 >= b0.w && m >= mlo0 && m <= mhi0;
-    const bool f1 = t1 >= b1.w && m >= mlo1 && m <= mhi1;
-    const float d0 = f0 ? fmaf(t0, t0, a0.w) : 1.0f, d1 = f1 ? fmaf(t1, t1, a1.w) : 1.0f;
-    const float n0 = f0 ? fmaf(t0, b0.x, b0.y) : 0.0f, n1 = f1 ? fmaf(t1, b1.x, b1.y) : 0.0f;
-    acc[m] = fmaf(fmaf(n1, d0, n0 * d1), rox_rcp(d0 * d1), acc[m]);
   }
 }
 
-// Pass 2 for a line whose slow zone meets the span: exactly the points pass 1 masked out
-// (t < t_z on the same rounded t, inside the window), with the full FP32 Faddeeva forms.
+// Pass 1 for the line in slot s alone (the last of an odd count), window-masked per sub-span
+// and point.
+template <bool NU>
+__device__ __forceinline__ void edge_line(const PairTab& P, const LineTab& L, int s, int Aw, int lane, float lanef,
+                                          float dnu_f, const float2* D, float (&acc)[ROX_K]) {
+  const int k = s >> 1, h = s & 1;
+  const float4 ab = P.ab[k], pq = P.pq[k], ef = P.ef[k];
+  const float A = row_lo(ab, h), B = row_hi(ab, h), Pc = row_lo(pq, h), Qc = row_hi(pq, h);
+  const float e = row_lo(ef, h), f = row_hi(ef, h);
+  const float tz = h ? P.tz[k].y : P.tz[k].x;
+  const int2 w = L.W[s];
+  const float X0 = NU ? 0.0f : fmaf(lanef + e, dnu_f, f);
+#pragma unroll
+  for (int m = 0; m < ROX_K; m++) {
+    const int am = Aw + 32 * m, bm = am + 31;
+    if (bm < w.x || am > w.y) continue;
+    const int j = am + lane;
+    const float x = pos<NU>(m, X0, e, f, D, dnu_f);
+    const float t = fmaxf(fmaf(x, x, A), tz);
+    const float v = fmaf(t, Pc, Qc) * rox_rcp(fmaf(t, t, B));
+    acc[m] += (j >= w.x && j <= w.y) ? v : 0.0f;
+  }
+}
+
+// Pass 2 for the line in slot s, whose slow zone meets the span: at exactly the points where
+// pass 1 clamped t (t < t_z on the same rounded t, inside the window), the full FP32 Faddeeva
+// forms replace the far form's boundary value that pass 1 added there: + S V - cf.
 // A zone of |z| < 6.5 takes the core forms at every point (rox_re_w_core holds 9e-6 out to
 // |z| = 7.1); on a uniform grid the lanes then take consecutive points of the zone rather than
 // aligned 32-point sub-spans (fewer, fuller warp steps). Otherwise, per 32-point sub-span, one
@@ -176,46 +266,46 @@ __device__ __forceinline__ void edge_pair(const Rec& r0, const Rec& r1, int Aw, 
 // further out), else rox_re_w per point. Accumulated into the warp's shared-memory row zacc
 // (one add per line and point; within a warp step the lanes touch distinct points).
 template <bool NU>
-__device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float Jf, float dnu_f, const float* daw,
-                                          const float2* D, float* zacc) {
-  const float X0 = fmaf(Jf - rq.a.x, dnu_f, -rq.a.y);
-  const int jlo = __float_as_int(rq.c.x), jhi = __float_as_int(rq.c.y);
-  const int zlo = __float_as_int(rq.c.z), zhi = __float_as_int(rq.c.w);
-  const int lo = max(max(zlo, jlo), Aw), hi = min(min(zhi, jhi), Aw + ROX_SPAN - 1);
+__device__ __forceinline__ void zone_line(const PairTab& P, const LineTab& L, int s, int Aw, int lane, float lanef,
+                                          float dnu_f, float inv_dnu, const float* daw, const float2* D, float* zacc) {
+  const int k = s >> 1, h = s & 1;
+  const float4 ab = P.ab[k], ef = P.ef[k];
+  const float A = row_lo(ab, h), e = row_lo(ef, h), f = row_hi(ef, h);
+  const float tz = h ? P.tz[k].y : P.tz[k].x;
+  const int2 w = L.W[s], z = L.Z[s];
+  const int lo = max(max(z.x, w.x), Aw), hi = min(min(z.y, w.y), Aw + ROX_SPAN - 1);
   if (lo > hi) return;
-  const float invG = rq.d.x, y = rq.d.y, pcore = rq.d.z;
-  if (!NU && rq.d.w != 0.0f) {
+  const float iGs = L.iG[s], y = L.y[s], pcore = L.pc[s], cf = L.cf[s];
+  const float invG = fabsf(iGs);
+  if (!NU && iGs < 0.0f) {
     // lanes on consecutive points of [lo, hi]; t rounded exactly as pass 1 rounds it
-    for (int k = lane; k <= hi - lo; k += 32) {
-      const int q = lo - Aw + k;
-      const float X0q = fmaf((float)(Aw + (q & 31)) - rq.a.x, dnu_f, -rq.a.y);
+    for (int q = lo - Aw + lane; q <= hi - Aw; q += 32) {
+      const float X0q = fmaf((float)(q & 31) + e, dnu_f, f);
       const float Xm = fmaf((float)(q & ~31), dnu_f, X0q);
-      const float t = fmaf(Xm, Xm, rq.a.z);
-      if (!(t < rq.b.w)) continue;
-      const float X = fmaf((float)(Aw + q) - rq.a.x, dnu_f, -rq.a.y);
-      zacc[q] += pcore * rox_re_w_core(daw, fabsf(X) * invG, y);
+      if (!(fmaf(Xm, Xm, A) < tz)) continue;
+      const float X = fmaf((float)q + e, dnu_f, f);
+      zacc[q] += fmaf(pcore, rox_re_w_core(daw, fabsf(X) * invG, y), -cf);
     }
     return;
   }
-  if (rq.d.w != 0.0f) {
+  const float X0 = NU ? 0.0f : fmaf(lanef + e, dnu_f, f);
+  if (iGs < 0.0f) {
     for (int m = (lo - Aw) >> 5; m <= ((hi - Aw) >> 5); m++) {
       const int j = Aw + 32 * m + lane;
-      const float Xm = pos<NU>(m, X0, rq.a, D, dnu_f);
-      const float t = fmaf(Xm, Xm, rq.a.z);
-      if (!(t < rq.b.w) || j < jlo || j > jhi) continue;
+      const float Xm = pos<NU>(m, X0, e, f, D, dnu_f);
+      if (!(fmaf(Xm, Xm, A) < tz) || j < w.x || j > w.y) continue;
       // the uniform grid recomputes X from the index in one rounding; node offsets are exact already
-      const float X = NU ? Xm : fmaf((float)j - rq.a.x, dnu_f, -rq.a.y);
-      zacc[32 * m + lane] += pcore * rox_re_w_core(daw, fabsf(X) * invG, y);
+      const float X = NU ? Xm : fmaf((float)(32 * m + lane) + e, dnu_f, f);
+      zacc[32 * m + lane] += fmaf(pcore, rox_re_w_core(daw, fabsf(X) * invG, y), -cf);
     }
     return;
   }
-  const float centre = rq.a.x + rq.a.y / dnu_f;     // k0 + f, within 0.25 grid steps (uniform grid)
+  const float centre = (float)Aw - e - f * inv_dnu;     // k0 + f, within 0.25 grid steps (uniform grid)
   const float y2 = y * y;
   for (int m = (lo - Aw) >> 5; m <= ((hi - Aw) >> 5); m++) {
     const int am = Aw + 32 * m, bm = am + 31;
     const int j = am + lane;
-    const float Xm = pos<NU>(m, X0, rq.a, D, dnu_f);
-    const float t = fmaf(Xm, Xm, rq.a.z);
+    const float Xm = pos<NU>(m, X0, e, f, D, dnu_f);
     float xm;   // |X| of the sub-span's point nearest the line centre, in units of gamma_G
     if constexpr (NU) {
       const float Xa = __shfl_sync(0xffffffffu, Xm, 0), Xb = __shfl_sync(0xffffffffu, Xm, 31);
@@ -225,15 +315,15 @@ __device__ __forceinline__ void zone_line(const Rec& rq, int Aw, int lane, float
                            ? 0.0f : fminf(fabsf((float)am - centre), fabsf((float)bm - centre));
       xm = fmaxf(dc - 1.0f, 0.0f) * dnu_f * invG;
     }
-    if (!(t < rq.b.w) || j < jlo || j > jhi) continue;
+    if (!(fmaf(Xm, Xm, A) < tz) || j < w.x || j > w.y) continue;
     const float sm = fmaf(xm, xm, y2);
-    const float X = NU ? Xm : fmaf((float)j - rq.a.x, dnu_f, -rq.a.y);
+    const float X = NU ? Xm : fmaf((float)(32 * m + lane) + e, dnu_f, f);
     const float x = fabsf(X) * invG;
     float r;
     if (sm >= ROX_S_CF3) r = rox_re_w_cf3(x, y);
     else if (sm >= ROX_S_CF5) r = rox_re_w_cf5g(x, y);
     else r = rox_re_w(daw, x, y);
-    zacc[32 * m + lane] += pcore * r;
+    zacc[32 * m + lane] += fmaf(pcore, r, -cf);
   }
 }
 
@@ -250,7 +340,8 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
   extern __shared__ float2 s_nodes[];
   __shared__ float4 s_geo[ROX_WARPS][2][32];
   __shared__ float s_S[ROX_WARPS][2][32];
-  __shared__ Rec s_rec[ROX_WARPS][32];
+  __shared__ PairTab s_pairs[ROX_WARPS];
+  __shared__ LineTab s_lines[ROX_WARPS];
   __shared__ float s_zacc[ROX_WARPS][ROX_SPAN];
   __shared__ float s_tot[ROX_WARPS][ROX_SPAN];    // the span's sum over its parts
   __shared__ float s_daw[ROX_NDAW];
@@ -265,7 +356,9 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
 
   float4(*geo_st)[32] = s_geo[w];
   float(*S_st)[32] = s_S[w];
-  Rec* rec = s_rec[w];
+  PairTab& PT = s_pairs[w];
+  LineTab& LT = s_lines[w];
+  const float lanef = (float)lane;
   float* zacc = s_zacc[w];
   float* stot = s_tot[w];
   float2* Drow = NU ? s_nodes + w * ROX_SPAN : nullptr;   // this span's node offsets
@@ -300,7 +393,6 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
     const float margin_cm = NU ? 0.0f : ROX_FAST_MARGIN * 32.0f * (ROX_K - 1) * dnu_f;
     const int Aw = span * ROX_SPAN;
     const int Bw = Aw + ROX_SPAN - 1;
-    const float Jf = (float)(Aw + lane);
     if (*Lst.status != ROX_OK) continue;           // list not prepared from sorted lines
     float bh = 0.f, bl = 0.f, Ws = 0.f;             // span's first node; offset of its last node
     if constexpr (NU) {
@@ -355,13 +447,18 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         cp_async_commit();
         cp_async_wait1();   // this lane's copies of the current batch have landed
 
-        // ---- per-line constants (lane <-> line b0 + lane)
-        Rec r;
-        if (lane < cnt) {
+        // ---- per-line constants (lane <-> line b0 + lane), written to the line's slot
+        const bool live = lane < cnt;
+        bool covers = false, zoned = false;
+        float ax = 0.f, ay = 0.f, vA = 1.f, vB = 0.f, vP = 0.f, vQ = 0.f, tz = 0.f, iGs = 1.f, yv = 0.f, pcv = 0.f;
+        float cfv = 0.f;
+        int jlo = 1, jhi = 0, zlo = 0, zhi = -1;
+        if (live) {
           const float4 g = geo_st[buf][lane];
           const float Sp = S_st[buf][lane];
-          const int jlo = __float_as_int(g.z), jhi = __float_as_int(g.w);
-          float nu0f, ax, ay;   // line centre; its offset state {k0, f dnu} or {c hi, c lo}
+          jlo = __float_as_int(g.z);
+          jhi = __float_as_int(g.w);
+          float nu0f;   // line centre; its offset state {E, F} (uniform grid) or {c hi, c lo} (nodes)
           if constexpr (NU) {
             // c = nu0 - (span's first node) as a double-float pair (the hi parts cancel exactly)
             nu0f = g.x;
@@ -370,25 +467,23 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             ay = cl - (ax - ch);
           } else {
             nu0f = Lst.nu_min_f + fmaf(g.x, dnu_f, g.y);
-            ax = g.x;
-            ay = g.y;
+            ax = (float)Aw - g.x;     // exact: both are integers below 2^24
+            ay = -g.y;
           }
           const float gG = nu0f * J.gG_fac;
           const float gL = BRD ? fmaf(gref, J.p_fac, nt) : gref * exp2f(nt * J.l2_ratio) * J.p_fac;
-          const long long ov = min((long long)jhi, whi) - max((long long)jlo, wlo) + 1;
-          if (ov > 0) evals += (unsigned long long)ov;
+          const int ov = min(jhi, (int)whi) - max(jlo, (int)wlo) + 1;
+          if (ov > 0) evals += (unsigned)ov;
           const float gG2 = gG * gG, gL2 = gL * gL;
           const float pY = Sp * gL * ROX_INV_PI;
-          const float invG = 1.0f / gG;
-          const float yv = gL * invG;
+          const float invG = rox_rcp(gG);
+          yv = gL * invG;
           const rox_far fc = rox_far_coefs(yv);      // far-zone form of this line (rox_faddeeva.cuh)
           // slow zone: |X| < sqrt(r2 gamma_G^2 - gamma_L^2), at least the precision margin
           float hz = sqrtf(fmaxf(0.0f, fc.r2 * gG2 - gL2));
           // zone |z| < 6.5 not widened by the margin: the core forms cover all of it
           const bool core_only = fc.r2 == ROX_S_PADE && hz >= margin_cm;
           hz = fmaxf(hz, margin_cm);
-          int zlo, zhi;
-          bool zoned;
           if constexpr (NU) {
             // the span's offsets run from -c to Ws - c; pass 2 then scans the window itself
             const float hzp = hz * 1.001f + 1e-6f * (fabsf(ax) + Ws);
@@ -396,110 +491,70 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             zlo = jlo;
             zhi = jhi;
           } else {
-            const int k0 = (int)g.x;
-            const float hzg = fminf(hz / dnu_f * 1.0001f, 8.0e6f);
-            const float f = g.y / dnu_f;
-            zlo = k0 + (int)floorf(f - hzg) - 1;
-            zhi = k0 + (int)ceilf(f + hzg) + 1;
+            // grid indices of the zone, |j - (k0 + f)| < hz / dnu, widened by 1e-4 relative and
+            // one point on each side (covers every point with t < t_z despite the roundings)
+            const int k0 = Aw - (int)ax;
+            const float hzg = fminf(hz * Lst.inv_dnu_f * 1.0001f, 8.0e6f);
+            const float fr = g.y * Lst.inv_dnu_f;
+            zlo = k0 + (int)floorf(fr - hzg) - 1;
+            zhi = k0 + (int)ceilf(fr + hzg) + 1;
             zoned = !(Bw < zlo || Aw > zhi);
           }
-          const bool covers = Aw >= jlo && Bw <= jhi;
-          const float vg = fc.alpha * gG2;
-          r.a = make_float4(ax, ay, vg, fc.beta * (gG2 * gG2));
-          r.b = make_float4(pY, pY * (fc.kappa * gG2), __uint_as_float((covers ? 1u : 0u) | (zoned ? 2u : 0u)),
-                            fmaf(hz, hz, vg));
-          r.c = make_float4(g.z, g.w, __int_as_float(zlo), __int_as_float(zhi));
-          r.d = make_float4(invG, yv, Sp * invG * ROX_INV_SQRT_PI, core_only ? 1.0f : 0.0f);
-        } else {   // padding record: contributes nothing
-          r.a = make_float4(0.f, 0.f, 1.f, 0.f);
-          r.b = make_float4(0.f, 0.f, __uint_as_float(0u), 0.f);
-          r.c = make_float4(__int_as_float(1), __int_as_float(0), __int_as_float(0), __int_as_float(0));
-          r.d = make_float4(1.f, 0.f, 0.f, 0.f);
+          covers = Aw >= jlo && Bw <= jhi;
+          vA = fc.alpha * gG2;
+          vB = fc.beta * (gG2 * gG2);
+          vP = pY;
+          vQ = pY * (fc.kappa * gG2);
+          tz = fmaf(hz, hz, vA);
+          iGs = core_only ? -invG : invG;
+          pcv = Sp * invG * ROX_INV_SQRT_PI;
+          if (zoned) cfv = fmaf(tz, vP, vQ) * rox_rcp(fmaf(tz, tz, vB));
         }
-        rec[lane] = r;
+        const unsigned clean = __ballot_sync(0xffffffffu, live && covers && !zoned);
+        const unsigned czone = __ballot_sync(0xffffffffu, live && covers && zoned);
+        const unsigned edge = __ballot_sync(0xffffffffu, live && !covers);
+        const int nclean = __popc(clean), ncov = nclean + __popc(czone);
+        const unsigned below = (1u << lane) - 1u;
+        const int slot = !covers ? ncov + __popc(edge & below)
+                                 : (zoned ? nclean + __popc(czone & below) : __popc(clean & below));
+        const unsigned zslots = __reduce_or_sync(0xffffffffu, (live && zoned) ? (1u << slot) : 0u);
+        if (live) {
+          const int k = slot >> 1, h = slot & 1;
+          float* ab = reinterpret_cast<float*>(&PT.ab[k]);
+          float* pq = reinterpret_cast<float*>(&PT.pq[k]);
+          float* ef = reinterpret_cast<float*>(&PT.ef[k]);
+          ab[h] = vA;
+          ab[2 + h] = vB;
+          pq[h] = vP;
+          pq[2 + h] = vQ;
+          ef[h] = ax;
+          ef[2 + h] = ay;
+          reinterpret_cast<float*>(&PT.tz[k])[h] = tz;
+          LT.W[slot] = make_int2(jlo, jhi);
+          LT.Z[slot] = make_int2(zlo, zhi);
+          LT.iG[slot] = iGs;
+          LT.y[slot] = yv;
+          LT.pc[slot] = pcv;
+          LT.cf[slot] = cfv;
+        }
         gref = gref_n;
         nt = nt_n;
         __syncwarp();
 
-        // ---- pass 1: far formula. Clean lines (window covers the span, no slow zone in it) in
-        // unmasked pairs; covering lines with a slow zone in masked pairs; window-edge lines in
-        // pairs with window masks. The orders are fixed, so the sum is reproducible.
-        const unsigned cls = __float_as_uint(r.b.z);
-        const bool live = lane < cnt;
-        unsigned cmask = __ballot_sync(0xffffffffu, live && cls == 1u);
-        unsigned zmask = __ballot_sync(0xffffffffu, live && cls == 3u);
-        const unsigned emask = __ballot_sync(0xffffffffu, live && !(cls & 1u));
-        const unsigned pmask = __ballot_sync(0xffffffffu, live && (cls & 2u));
-        while (cmask) {
-          const int i0 = __ffs(cmask) - 1;
-          cmask &= cmask - 1;
-          const float4 a0 = rec[i0].a, b0v = rec[i0].b;
-          const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y);
-          if (cmask) {
-            const int i1 = __ffs(cmask) - 1;
-            cmask &= cmask - 1;
-            const float4 a1 = rec[i1].a, b1v = rec[i1].b;
-            const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
-#pragma unroll
-            for (int m = 0; m < ROX_K; m++) {
-              const float x0 = pos<NU>(m, X0, a0, D, dnu_f);
-              const float x1 = pos<NU>(m, X1, a1, D, dnu_f);
-              const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
-              const float d0 = fmaf(t0, t0, a0.w), d1 = fmaf(t1, t1, a1.w);
-              const float n0 = fmaf(t0, b0v.x, b0v.y), n1 = fmaf(t1, b1v.x, b1v.y);
-              const float dd = d0 * d1;
-              const float nn = fmaf(n1, d0, n0 * d1);
-              acc[m] = fmaf(nn, rox_rcp(dd), acc[m]);
-            }
-          } else {
-#pragma unroll
-            for (int m = 0; m < ROX_K; m++) acc[m] += far_term(pos<NU>(m, X0, a0, D, dnu_f), a0, b0v);
-          }
+        // ---- pass 1: far formula at every point of every line's window. Clean pairs as they
+        // are; pairs with a zoned line with t clamped to the zone boundary; then the rest (an odd
+        // covering line, the window-edge lines) in pairs with window masks. Fixed orders: the sum
+        // is reproducible.
+        const int kc = nclean >> 1, kz = ncov >> 1;
+        for (int k = 0; k < kc; k++) cover_pair<NU, false>(PT, k, lanef, dnu_f, D, acc);
+        for (int k = kc; k < kz; k++) cover_pair<NU, true>(PT, k, lanef, dnu_f, D, acc);
+        for (int s2 = 2 * kz; s2 < cnt; s2 += 2) {
+          if (s2 + 1 < cnt) edge_pair<NU>(PT, LT, s2 >> 1, Aw, lane, lanef, dnu_f, D, acc);
+          else edge_line<NU>(PT, LT, s2, Aw, lane, lanef, dnu_f, D, acc);
         }
-        while (zmask) {
-          const int i0 = __ffs(zmask) - 1;
-          zmask &= zmask - 1;
-          const float4 a0 = rec[i0].a, b0v = rec[i0].b;
-          const float X0 = fmaf(Jf - a0.x, dnu_f, -a0.y);
-          if (zmask) {
-            const int i1 = __ffs(zmask) - 1;
-            zmask &= zmask - 1;
-            const float4 a1 = rec[i1].a, b1v = rec[i1].b;
-            const float X1 = fmaf(Jf - a1.x, dnu_f, -a1.y);
-#pragma unroll
-            for (int m = 0; m < ROX_K; m++) {
-              const float x0 = pos<NU>(m, X0, a0, D, dnu_f);
-              const float x1 = pos<NU>(m, X1, a1, D, dnu_f);
-              const float t0 = fmaf(x0, x0, a0.z), t1 = fmaf(x1, x1, a1.z);
-              const bool f0 = t0 >= b0v.w, f1 = t1 >= b1v.w;   // outside the slow zone
-              const float d0 = f0 ? fmaf(t0, t0, a0.w) : 1.0f, d1 = f1 ? fmaf(t1, t1, a1.w) : 1.0f;
-              const float n0 = f0 ? fmaf(t0, b0v.x, b0v.y) : 0.0f;
-              const float n1 = f1 ? fmaf(t1, b1v.x, b1v.y) : 0.0f;
-              const float dd = d0 * d1;
-              const float nn = fmaf(n1, d0, n0 * d1);
-              acc[m] = fmaf(nn, rox_rcp(dd), acc[m]);
-            }
-          } else {
-#pragma unroll
-            for (int m = 0; m < ROX_K; m++) acc[m] += masked_far(pos<NU>(m, X0, a0, D, dnu_f), a0, b0v);
-          }
-        }
-        for (unsigned em = emask; em;) {
-          const int i0 = __ffs(em) - 1;
-          em &= em - 1;
-          if (!em) {
-            edge_line<NU>(rec[i0].a, rec[i0].b, rec[i0].c, Aw, lane, Jf, dnu_f, D, acc);
-            break;
-          }
-          const int i1 = __ffs(em) - 1;
-          em &= em - 1;
-          edge_pair<NU>(rec[i0], rec[i1], Aw, lane, Jf, dnu_f, D, acc);
-        }
-        // ---- pass 2: the points each zoned line left out of pass 1, full Faddeeva forms
-        for (unsigned pm = pmask; pm; pm &= pm - 1) {
-          const Rec rq = rec[__ffs(pm) - 1];
-          zone_line<NU>(rq, Aw, lane, Jf, dnu_f, s_daw, D, zacc);
-        }
+        // ---- pass 2: at the points each zoned line had clamped, the full Faddeeva forms
+        for (unsigned z = zslots; z; z &= z - 1)
+          zone_line<NU>(PT, LT, __ffs(z) - 1, Aw, lane, lanef, dnu_f, Lst.inv_dnu_f, s_daw, D, zacc);
         __syncwarp();
         // compensated (Kahan) accumulation of the partial sums, every 4 batches
         if ((nb & 3) == 3 || b0 + 32 >= phi) {
