@@ -407,8 +407,9 @@ int rox_fp32_probe(int n_blocks, int reps, float* out, size_t out_bytes, double*
  * rox_xsec; status_out (device, 1 x int32, may be NULL) receives the call's device-side
  * status (ROX_OK, or ROX_EUNSORTED with sigma_out untouched), stream-ordered.
  * No cudaMalloc, cudaFree or other allocation is made. The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress); make that first call before any
- * stream capture. All calls share the one array: calls that overlap on the GPU (different
+ * up the array's device address (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture. A cudaDeviceReset unloads the
+ * array: after one, restart the process before calling this entry point again. All calls share the one array: calls that overlap on the GPU (different
  * streams, or different host threads, on one device) race and corrupt each other's results;
  * serialise them. Each call clears the parts of the array that must start at zero. */
 #define ROX_STATIC_MAX_LINES 262144

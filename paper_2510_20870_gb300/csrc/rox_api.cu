@@ -159,7 +159,7 @@ struct WsLayout {
 };
 
 WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, bool nodes = false,
-                   long long n_bins = 0, bool broad = false) {
+                   long long n_bins = 0, bool broad = false, long long tail_max = ROX_TAIL_ITEMS_MAX) {
   WsLayout w;
   char* base = (char*)ws;
   size_t off = 0;
@@ -176,7 +176,7 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, b
   off += rox_align256((size_t)n_temps * (size_t)(n_lines > 0 ? n_lines : 1) * 8);
   w.S32 = (float*)(base + off);
   off += rox_align256((size_t)n_temps * (size_t)(n_lines > 0 ? n_lines : 1) * 4);
-  w.tail_cap = nt < ROX_TAIL_ITEMS_MAX ? nt : ROX_TAIL_ITEMS_MAX;
+  w.tail_cap = nt < tail_max ? nt : tail_max;
   w.tail_part = (float*)(base + off);
   w.tail_cnt = (int32_t*)(base + off + rox_align256((size_t)w.tail_cap * ROX_PARTS * ROX_SPAN * sizeof(float)));
   off += rox_tail_bytes(w.tail_cap);
@@ -327,8 +327,11 @@ int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* job
       A.item_end[k] = items;
     }
     const int blocks = items < nblocks ? items : nblocks;
-    long long split = (long long)blocks * ROX_WARPS / 2;
-    if (split > items / 2) split = items / 2;
+    // whole items in complete rounds of the launch's warps, then at least one round of items in
+    // parts, so the launch ends in pieces of 1/ROX_PARTS of an item
+    const long long warps = (long long)blocks * ROX_WARPS;
+    long long split = items <= warps ? items : items % warps + warps;
+    if (split > items) split = items;
     if (split > tail_cap) split = tail_cap;
     A.n_jobs = nj;
     A.n_items = items;
@@ -439,7 +442,8 @@ namespace {
 int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_nodes* nodes, int n_pt,
                     const double* P_bar, const double* T, const double* Q_T, double Q_ref, double mass_amu,
                     double cutoff, unsigned flags, float* sigma_out, void* ws, size_t ws_bytes, void* stream,
-                    const rox_select* sel = nullptr, const rox_broadening* br = nullptr) {
+                    const rox_select* sel = nullptr, const rox_broadening* br = nullptr,
+                    long long tail_max = ROX_TAIL_ITEMS_MAX) {
   int rc = check_lines(lines, true, br == nullptr);
   if (rc) return rc;
   RoxBroadDev bdev;
@@ -474,7 +478,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   }
   const int n_temps = (int)temps.size();
   if (!ws || ((uintptr_t)ws & 255)) return fail(ROX_EINVAL, "workspace NULL or not 256-byte aligned");
-  WsLayout w = ws_layout(ws, lines->n, n_grid, n_temps, on_nodes, n_bins, br != nullptr);
+  WsLayout w = ws_layout(ws, lines->n, n_grid, n_temps, on_nodes, n_bins, br != nullptr, tail_max);
   if (ws_bytes < w.bytes) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.bytes);
 
   cudaStream_t s = (cudaStream_t)stream;
@@ -721,6 +725,26 @@ int rox_node_windows(const double* nu0_sorted, int64_t n_lines, const rox_nodes*
                                             nullptr, nullptr, 0, (cudaStream_t)stream),
                     "node windows kernel") ? ROX_ECUDA : ok();
 }
+
+}  // extern "C"
+
+// rox_xsec with the tail scratch limited to tail_max items (library-internal, C++ linkage:
+// rox_xsec_static runs in a fixed 16 MiB array), and the workspace size that goes with it
+size_t rox_xsec_workspace_size_tail(int64_t n_lines, const rox_grid* grid, long long tail_max) {
+  if (!grid || grid->n <= 0 || n_lines < 0) return 0;
+  return ws_layout(nullptr, n_lines, grid->n, 1, false, 0, false, tail_max).bytes;
+}
+int rox_xsec_tail(const rox_lines* lines, const rox_grid* grid, double P_bar, double T, double Q_T, double Q_ref,
+                  double mass_amu, double cutoff, float* sigma_out, void* ws, size_t ws_bytes, void* stream,
+                  long long tail_max) {
+  int rc;
+  if ((rc = check_grid(grid))) return rc;
+  if ((rc = check_cutoff(cutoff, grid))) return rc;
+  return xsec_batch_impl(lines, grid, nullptr, 1, &P_bar, &T, &Q_T, Q_ref, mass_amu, cutoff, 0u, sigma_out, ws,
+                         ws_bytes, stream, nullptr, nullptr, tail_max);
+}
+
+extern "C" {
 
 int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double T, double Q_T, double Q_ref,
              double mass_amu, double cutoff, float* sigma_out, void* ws, size_t ws_bytes, void* stream) {

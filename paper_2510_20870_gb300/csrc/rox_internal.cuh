@@ -113,13 +113,15 @@ struct RoxJobDev {
 };
 
 // Every span's lines are summed as ROX_PARTS consecutive parts (batch-aligned), each from
-// zero, and the part sums are added in part order. A work item is normally a whole span;
-// the last items of a launch (at most ROX_TAIL_ITEMS_MAX, about half a warp round) are
-// split into their parts, taken by different warps: each part stores its sum in the tail
-// scratch and the last of them to finish adds the parts in the same order. The result is
-// the same either way, so it depends neither on the split nor on the launch grid.
-#define ROX_PARTS 4
-#define ROX_TAIL_ITEMS_MAX 2048
+// zero, and the part sums are added in part order. A work item is normally a whole span; the
+// last items of a launch are split into their parts, taken by different warps: each part stores
+// its sum in the tail scratch and the last of them to finish adds the parts in the same order.
+// The result is the same either way, so it depends neither on the split nor on the launch grid.
+// How many items are split is chosen per launch so that the whole items fill complete rounds of
+// the launch's warps and the split ones end the launch in pieces of 1/ROX_PARTS of an item
+// (at most ROX_TAIL_ITEMS_MAX items, the size of the workspace's tail scratch).
+#define ROX_PARTS 16
+#define ROX_TAIL_ITEMS_MAX 8192
 
 struct RoxVoigtArgs {
   RoxWsHeader* hdr;

@@ -16,6 +16,16 @@
 static __device__ __align__(256) unsigned char rox_static_scratch[ROX_STATIC_BYTES];
 
 int rox_set_error(int code, const char* msg);   // rox_api.cu
+// rox_xsec with the tail scratch (the split work items of the Voigt launch) limited to
+// tail_max items, and its workspace size (rox_api.cu)
+int rox_xsec_tail(const rox_lines* lines, const rox_grid* grid, double P_bar, double T, double Q_T, double Q_ref,
+                  double mass_amu, double cutoff, float* sigma_out, void* ws, size_t ws_bytes, void* stream,
+                  long long tail_max);
+size_t rox_xsec_workspace_size_tail(int64_t n_lines, const rox_grid* grid, long long tail_max);
+
+// Split work items the static scratch has room for (16 KB each); the launch splits fewer items
+// than usual, which changes how its warps share the last items, not the result.
+#define ROX_STATIC_TAIL_ITEMS 256
 
 namespace {
 
@@ -24,7 +34,8 @@ void* g_static_ptr[ROX_STATIC_MAX_DEVICES] = {nullptr};
 
 // Device address of the scratch array on the current device. In host code the array's
 // name is only a host-side stand-in, so the address is looked up once per device, with
-// that device current, and cached.
+// that device current, and cached. The cache outlives a cudaDeviceReset (which unloads the
+// array): after a reset the process must be restarted before this entry point is used again.
 int static_scratch(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -55,10 +66,13 @@ extern "C" int rox_xsec_static(const rox_lines* lines, const rox_grid* grid, dou
              ROX_STATIC_MAX_LINES, ROX_STATIC_MAX_GRID);
     return rox_set_error(ROX_ERANGE, msg);
   }
+  if (rox_xsec_workspace_size_tail(lines->n, grid, ROX_STATIC_TAIL_ITEMS) > ROX_STATIC_BYTES)
+    return rox_set_error(ROX_ERANGE, "rox_xsec_static: the problem does not fit the static scratch");
   void* ws = nullptr;
   int rc = static_scratch(&ws);
   if (rc) return rc;
-  rc = rox_xsec(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, ROX_STATIC_BYTES, stream);
+  rc = rox_xsec_tail(lines, grid, P_bar, T, Q_T, Q_ref, mass_amu, cutoff, sigma_out, ws, ROX_STATIC_BYTES, stream,
+                     ROX_STATIC_TAIL_ITEMS);
   if (rc) return rc;
   if (status_out) {
     // device-side status of this call (ROX_OK, or ROX_EUNSORTED with sigma untouched)

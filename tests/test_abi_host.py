@@ -96,12 +96,21 @@ def test_partition_function_host_helper():
     assert PartitionFunction(("analytic", 0.05))(400.0) == pytest.approx(0.05 * 8000.0)
 
 
-def test_static_scratch_holds_the_largest_static_problem():
-    """rox_xsec_static runs rox_xsec in a fixed 16 MiB array: the workspace of its largest
-    accepted problem (ROX_STATIC_MAX_LINES lines, ROX_STATIC_MAX_GRID points, one T) fits."""
+@host_only
+def test_static_scratch_holds_the_largest_static_problem(lib):
+    """rox_xsec_static runs the cross-section in a fixed 16 MiB array: its largest accepted
+    problem (ROX_STATIC_MAX_LINES lines, ROX_STATIC_MAX_GRID points) passes the size checks and
+    only then meets the missing GPU (ROX_ECUDA); one line more is refused with ROX_ERANGE. The
+    pointers are placeholders that are never dereferenced."""
     from paper_2510_20870_gb300 import _binding as b
-    need = b.rox_xsec_workspace_size(262144, (0.0, 0.01, 1 << 21), 1)
-    assert 0 < need <= 16 << 20, need
+    fn = b.lib.rox_xsec_static
+    grid = b.grid_struct((0.0, 0.01, 1 << 21))
+    for n, want in ((262144, b.ROX_ECUDA), (262145, b.ROX_ERANGE)):
+        L = b.RoxLines(ctypes.c_void_p(256), ctypes.c_void_p(512), None, ctypes.c_void_p(768), ctypes.c_void_p(1024),
+                       ctypes.c_void_p(1280), n, 0, 0)
+        rc = fn(ctypes.byref(L), ctypes.byref(grid), 1.0, 1000.0, 1.0, 1.0, 18.0, 25.0, ctypes.c_void_p(2048), None,
+                None)
+        assert rc == want, (n, rc, b.lib.rox_last_error())
 
 
 @host_only
