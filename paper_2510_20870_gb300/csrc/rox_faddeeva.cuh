@@ -59,6 +59,16 @@ ROX_FN float rox_rcp(float v) {
 #endif
 }
 
+ROX_FN float rox_rsqrt(float v) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+#else
+  return 1.0f / sqrtf(v);
+#endif
+}
+
 ROX_FN float rox_exp2(float v) {
 #ifdef __CUDA_ARCH__
   float r;

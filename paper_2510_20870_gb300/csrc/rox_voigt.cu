@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             ay = -g.y;
           }
           const float gG = nu0f * J.gG_fac;
-          const float gL = BRD ? fmaf(gref, J.p_fac, nt) : gref * exp2f(nt * J.l2_ratio) * J.p_fac;
+          const float gL = BRD ? fmaf(gref, J.p_fac, nt) : gref * rox_exp2(nt * J.l2_ratio) * J.p_fac;
           const int ov = min(jhi, (int)whi) - max(jlo, (int)wlo) + 1;
           if (ov > 0) evals += (unsigned)ov;
           const float gG2 = gG * gG, gL2 = gL * gL;
@@ -480,7 +480,9 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
           yv = gL * invG;
           const rox_far fc = rox_far_coefs(yv);      // far-zone form of this line (rox_faddeeva.cuh)
           // slow zone: |X| < sqrt(r2 gamma_G^2 - gamma_L^2), at least the precision margin
-          float hz = sqrtf(fmaxf(0.0f, fc.r2 * gG2 - gL2));
+          const float hz2 = fmaxf(0.0f, fc.r2 * gG2 - gL2);
+          float hz = hz2 * rox_rsqrt(hz2);            // 0 for hz2 = 0 (rsqrt(0) = inf, product taken as 0 below)
+          hz = hz2 > 0.0f ? hz : 0.0f;
           // zone |z| < 6.5 not widened by the margin: the core forms cover all of it
           const bool core_only = fc.r2 == ROX_S_PADE && hz >= margin_cm;
           hz = fmaxf(hz, margin_cm);
@@ -496,8 +498,8 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
             const int k0 = Aw - (int)ax;
             const float hzg = fminf(hz * Lst.inv_dnu_f * 1.0001f, 8.0e6f);
             const float fr = g.y * Lst.inv_dnu_f;
-            zlo = k0 + (int)floorf(fr - hzg) - 1;
-            zhi = k0 + (int)ceilf(fr + hzg) + 1;
+            zlo = k0 + __float2int_rd(fr - hzg) - 1;
+            zhi = k0 + __float2int_ru(fr + hzg) + 1;
             zoned = !(Bw < zlo || Aw > zhi);
           }
           covers = Aw >= jlo && Bw <= jhi;
