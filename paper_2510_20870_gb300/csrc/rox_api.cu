@@ -39,7 +39,8 @@ cudaError_t rox_launch_node_offsets(const double* nodes, long long n, long long 
                                     int32_t* status, int32_t bad_value, cudaStream_t s);
 void rox_fill_strength_consts(int convention, double T, double Q_T, double Q_ref, RoxStrengthJob* jb);
 cudaError_t rox_launch_strengths_jobs(const RoxStrengthJobs& J, long long max_count, cudaStream_t s);
-cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes);
+cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes, bool pre);
+cudaError_t rox_launch_line_params(const RoxListDev& L, const RoxJobDev& J, float4* rec, cudaStream_t s);
 cudaError_t rox_launch_select(const double* nu0, const double* S_T, long long n, int n_temps,
                               const unsigned long long* smax_bits, double origin, double width, long long n_bins,
                               double rel, int32_t* bin, unsigned long long* binmax_bits, float* S32, cudaStream_t s);
@@ -155,11 +156,13 @@ struct WsLayout {
   size_t compact_tmp_bytes;
   float* broad_G;      // broadening descriptions only: [n_temps][n_lines] broadeners' sums, [n_lines]
   float* broad_N;      //   natural widths
+  float4* rec;         // one temperature on a uniform grid: per line 3 float4 of per-line constants
   size_t bytes;
 };
 
 WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, bool nodes = false,
-                   long long n_bins = 0, bool broad = false, long long tail_max = ROX_TAIL_ITEMS_MAX) {
+                   long long n_bins = 0, bool broad = false, long long tail_max = ROX_TAIL_ITEMS_MAX,
+                   bool pre = true) {
   WsLayout w;
   char* base = (char*)ws;
   size_t off = 0;
@@ -229,6 +232,11 @@ WsLayout ws_layout(void* ws, long long n_lines, long long n_grid, int n_temps, b
     w.broad_N = (float*)(base + off);
     off += rox_align256(nl * 4);
   }
+  w.rec = nullptr;
+  if (pre && n_temps == 1 && !nodes && n_bins == 0 && !broad) {
+    w.rec = (float4*)(base + off);
+    off += rox_align256((size_t)(n_lines > 0 ? n_lines : 1) * 3 * sizeof(float4));
+  }
   w.bytes = off;
   return w;
 }
@@ -285,20 +293,21 @@ int select_bins(const rox_select* sel, const rox_grid* g, double cutoff, double*
   return ROX_OK;
 }
 
-int g_voigt_blocks[2] = {0, 0};
-int g_voigt_device[2] = {-1, -1};
+int g_voigt_blocks[3] = {0, 0, 0};
+int g_voigt_device[3] = {-1, -1, -1};
 
-// persistent grid of the Voigt kernel on the current device (uniform grid or nodes)
-int voigt_grid(int* out, bool nodes = false) {
+// persistent grid of the Voigt kernel on the current device (uniform grid, nodes, or the
+// instantiation with precomputed per-line constants)
+int voigt_grid(int* out, bool nodes = false, bool pre = false) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
-  const int v = nodes ? 1 : 0;
+  const int v = pre ? 2 : (nodes ? 1 : 0);
   if (dev != g_voigt_device[v]) {
     int sms = 0, per = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_check(e, "cudaDeviceGetAttribute");
-    e = rox_voigt_blocks_per_sm(&per, nodes);
+    e = rox_voigt_blocks_per_sm(&per, nodes, pre);
     if (e != cudaSuccess) return cuda_check(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     g_voigt_blocks[v] = sms * (per > 0 ? per : 1);
     g_voigt_device[v] = dev;
@@ -443,7 +452,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
                     const double* P_bar, const double* T, const double* Q_T, double Q_ref, double mass_amu,
                     double cutoff, unsigned flags, float* sigma_out, void* ws, size_t ws_bytes, void* stream,
                     const rox_select* sel = nullptr, const rox_broadening* br = nullptr,
-                    long long tail_max = ROX_TAIL_ITEMS_MAX) {
+                    long long tail_max = ROX_TAIL_ITEMS_MAX, bool allow_pre = true) {
   int rc = check_lines(lines, true, br == nullptr);
   if (rc) return rc;
   RoxBroadDev bdev;
@@ -478,12 +487,14 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   }
   const int n_temps = (int)temps.size();
   if (!ws || ((uintptr_t)ws & 255)) return fail(ROX_EINVAL, "workspace NULL or not 256-byte aligned");
-  WsLayout w = ws_layout(ws, lines->n, n_grid, n_temps, on_nodes, n_bins, br != nullptr, tail_max);
+  WsLayout w = ws_layout(ws, lines->n, n_grid, n_temps, on_nodes, n_bins, br != nullptr, tail_max, allow_pre);
+  // one (P,T) point on a uniform grid: the per-line constants once per line (k_line_params)
+  const bool pre = w.rec != nullptr && n_pt == 1 && lines->n > 0;
   if (ws_bytes < w.bytes) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.bytes);
 
   cudaStream_t s = (cudaStream_t)stream;
   int nblocks = 0;
-  if ((rc = voigt_grid(&nblocks, on_nodes))) return rc;
+  if ((rc = voigt_grid(&nblocks, on_nodes, pre))) return rc;
   const long long nt = n_tiles_of(n_grid);
   const long long nl = lines->n;
 
@@ -548,6 +559,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   L0.width_f16 = lines->width_dtype == ROX_WIDTH_F16;
   L0.idx = nullptr;
   L0.inv_dnu_f = on_nodes ? 0.0f : (float)(1.0 / grid->dnu);
+  L0.rec = pre ? w.rec : nullptr;
   std::vector<RoxJobDev> jobs(n_pt);
   for (int k = 0; k < n_pt; k++) {
     RoxJobDev& J = jobs[k];
@@ -590,7 +602,8 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
     }
     return ok();
   }
-  const int extras = br ? ROX_VX_BROAD : 0;
+  if (pre && (rc = cuda_check(rox_launch_line_params(L0, jobs[0], w.rec, s), "line parameter kernel"))) return rc;
+  const int extras = br ? ROX_VX_BROAD : (pre ? ROX_VX_PRE : 0);
   if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, w.tail_part, w.tail_cnt, w.tail_cap, nblocks, s,
                               on_nodes, extras)))
     return rc;
@@ -732,7 +745,7 @@ int rox_node_windows(const double* nu0_sorted, int64_t n_lines, const rox_nodes*
 // rox_xsec_static runs in a fixed 16 MiB array), and the workspace size that goes with it
 size_t rox_xsec_workspace_size_tail(int64_t n_lines, const rox_grid* grid, long long tail_max) {
   if (!grid || grid->n <= 0 || n_lines < 0) return 0;
-  return ws_layout(nullptr, n_lines, grid->n, 1, false, 0, false, tail_max).bytes;
+  return ws_layout(nullptr, n_lines, grid->n, 1, false, 0, false, tail_max, false).bytes;
 }
 int rox_xsec_tail(const rox_lines* lines, const rox_grid* grid, double P_bar, double T, double Q_T, double Q_ref,
                   double mass_amu, double cutoff, float* sigma_out, void* ws, size_t ws_bytes, void* stream,
@@ -741,7 +754,7 @@ int rox_xsec_tail(const rox_lines* lines, const rox_grid* grid, double P_bar, do
   if ((rc = check_grid(grid))) return rc;
   if ((rc = check_cutoff(cutoff, grid))) return rc;
   return xsec_batch_impl(lines, grid, nullptr, 1, &P_bar, &T, &Q_T, Q_ref, mass_amu, cutoff, 0u, sigma_out, ws,
-                         ws_bytes, stream, nullptr, nullptr, tail_max);
+                         ws_bytes, stream, nullptr, nullptr, tail_max, false);
 }
 
 extern "C" {
@@ -937,6 +950,7 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     L[l].nu_min_f = (float)P.lattice.nu_min;
     L[l].width_f16 = P.lines.width_dtype == ROX_WIDTH_F16;
     L[l].inv_dnu_f = (float)(1.0 / P.lattice.dnu);
+    L[l].rec = nullptr;
   }
   std::vector<RoxJobDev> J(n_jobs);
   for (int k = 0; k < n_jobs; k++) {

@@ -68,6 +68,10 @@ struct RoxListDev {
   // {nu0 hi, nu0 lo, jlo, jhi}
   const float2* node_d;
   const float2* span_base;
+  // precomputed per-line constants of the launch's one (P,T) point (ROX_VX_PRE lists, else NULL):
+  // per line 3 float4, {A, B, P, Q}, {t_z, 1/gamma_G (negative: core-only zone), y, S/(gamma_G
+  // sqrt(pi))}, {far form at t_z, zlo (int bits), zhi (int bits), 0}
+  const float4* rec;
   long long n_lattice;
   float dnu_f;
   float nu_min_f;
@@ -93,6 +97,7 @@ struct RoxBroadDev {
 // extras of a Voigt launch (kernel instantiations)
 #define ROX_VX_INDEX 1    // lists are subsets of the sorted lines given by an index (RoxListDev::idx)
 #define ROX_VX_BROAD 2    // widths from the broadening pass (RoxListDev::gLT, gN)
+#define ROX_VX_PRE 4      // per-line constants precomputed for the launch's one (P,T) point (RoxListDev::rec)
 
 struct RoxJobDev {
   const float* S32;                      // S * 2^-e of lines l0, l0+1, ... at this job's T

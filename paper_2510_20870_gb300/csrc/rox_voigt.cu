@@ -327,6 +327,77 @@ __device__ __forceinline__ void zone_line(const PairTab& P, const LineTab& L, in
   }
 }
 
+// Per-line constants of one (P,T) point that do not depend on the span: the far-form
+// constants, the slow zone's half-width hz (at least the precision margin) and threshold t_z,
+// and what pass 2 needs. nu0f: the line centre in FP32; Sp: S 2^-e; gref, nt: the width inputs
+// (see load_widths). The Voigt kernel computes them per line and span, or (ROX_VX_PRE) reads
+// them from k_line_params, which computes them once per line with this same function.
+struct LineK {
+  float A, B, P, Q, tz, iGs, y, pc, cf, hz;
+};
+template <bool BRD>
+__device__ __forceinline__ LineK line_consts(float nu0f, float Sp, float gref, float nt, const RoxJobDev& J,
+                                             float margin_cm, bool want_cf) {
+  LineK k;
+  const float gG = nu0f * J.gG_fac;
+  const float gL = BRD ? fmaf(gref, J.p_fac, nt) : gref * rox_exp2(nt * J.l2_ratio) * J.p_fac;
+  const float gG2 = gG * gG, gL2 = gL * gL;
+  const float pY = Sp * gL * ROX_INV_PI;
+  const float invG = rox_rcp(gG);
+  k.y = gL * invG;
+  const rox_far fc = rox_far_coefs(k.y);      // far-zone form of this line (rox_faddeeva.cuh)
+  // slow zone: |X| < sqrt(r2 gamma_G^2 - gamma_L^2), at least the precision margin
+  const float hz2 = fmaxf(0.0f, fc.r2 * gG2 - gL2);
+  float hz = hz2 * rox_rsqrt(hz2);            // 0 for hz2 = 0 (rsqrt(0) = inf, product taken as 0 below)
+  hz = hz2 > 0.0f ? hz : 0.0f;
+  // zone |z| < 6.5 not widened by the margin: the core forms cover all of it
+  const bool core_only = fc.r2 == ROX_S_PADE && hz >= margin_cm;
+  k.hz = fmaxf(hz, margin_cm);
+  k.A = fc.alpha * gG2;
+  k.B = fc.beta * (gG2 * gG2);
+  k.P = pY;
+  k.Q = pY * (fc.kappa * gG2);
+  k.tz = fmaf(k.hz, k.hz, k.A);
+  k.iGs = core_only ? -invG : invG;
+  k.pc = Sp * invG * ROX_INV_SQRT_PI;
+  k.cf = want_cf ? fmaf(k.tz, k.P, k.Q) * rox_rcp(fmaf(k.tz, k.tz, k.B)) : 0.0f;
+  return k;
+}
+
+// Grid indices of a line's slow zone on a uniform grid, |j - (k0 + f)| < hz / dnu, widened by 1e-4
+// relative and one point on each side (covers every point with t < t_z despite the roundings).
+// g: the line's geometry record {k0, f dnu, jlo, jhi}.
+__device__ __forceinline__ void zone_bounds(const float4& g, float hz, float inv_dnu, int& zlo, int& zhi) {
+  const int k0 = (int)g.x;
+  const float hzg = fminf(hz * inv_dnu * 1.0001f, 8.0e6f);
+  const float fr = g.y * inv_dnu;
+  zlo = k0 + __float2int_rd(fr - hzg) - 1;
+  zhi = k0 + __float2int_ru(fr + hzg) + 1;
+}
+
+// the uniform grid's precision margin of the slow zones (cm^-1; see ROX_FAST_MARGIN)
+__device__ __forceinline__ float fast_margin(float dnu_f) { return ROX_FAST_MARGIN * 32.0f * (ROX_K - 1) * dnu_f; }
+
+// k_line_params: the per-line constants of one job ((P,T) point) for lines [J.l0, J.l1) of a
+// uniform-grid list, once per line, for the ROX_VX_PRE Voigt launch (which otherwise recomputes
+// them in every span a line reaches). One thread per line, coalesced loads and 48-byte stores.
+__global__ void k_line_params(const RoxListDev L, const RoxJobDev J, float4* rec) {
+  const float margin_cm = fast_margin(L.dnu_f);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = J.l0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < J.l1; i += stride) {
+    const float4 g = L.geo[i];
+    const float Sp = J.S32[i - J.l0];
+    const float gref = load_width(L.gamma_ref, L.width_f16, i), nt = load_width(L.n_t, L.width_f16, i);
+    const float nu0f = L.nu_min_f + fmaf(g.x, L.dnu_f, g.y);
+    const LineK k = line_consts<false>(nu0f, Sp, gref, nt, J, margin_cm, true);
+    int zlo, zhi;
+    zone_bounds(g, k.hz, L.inv_dnu_f, zlo, zhi);
+    rec[3 * i] = make_float4(k.A, k.B, k.P, k.Q);
+    rec[3 * i + 1] = make_float4(k.tz, k.iGs, k.y, k.pc);
+    rec[3 * i + 2] = make_float4(k.cf, __int_as_float(zlo), __int_as_float(zhi), 0.0f);
+  }
+}
+
 // NU: the lists are on user-provided nodes (node offsets in dynamic shared memory, one
 // ROX_SPAN row of float2 per warp). X: ROX_VX_INDEX (each list is a subset of the sorted lines,
 // given by RoxListDev::idx, e.g. the kept lines of a main-contributor selection; span ranges
@@ -337,7 +408,8 @@ template <bool NU, int X>
 __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant__ RoxVoigtArgs A) {
   constexpr bool IDX = (X & ROX_VX_INDEX) != 0;
   constexpr bool BRD = (X & ROX_VX_BROAD) != 0;
-  extern __shared__ float2 s_nodes[];
+  constexpr bool PRE = (X & ROX_VX_PRE) != 0;
+  extern __shared__ __align__(16) float2 s_nodes[];   // NU: node offsets; PRE: the staged per-line constants
   __shared__ float4 s_geo[ROX_WARPS][2][32];
   __shared__ float s_S[ROX_WARPS][2][32];
   __shared__ PairTab s_pairs[ROX_WARPS];
@@ -362,6 +434,8 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
   float* zacc = s_zacc[w];
   float* stot = s_tot[w];
   float2* Drow = NU ? s_nodes + w * ROX_SPAN : nullptr;   // this span's node offsets
+  // PRE: per warp two buffers of 32 lines x 3 float4 of per-line constants
+  float4(*rec_st)[32][3] = PRE ? reinterpret_cast<float4(*)[32][3]>(s_nodes) + 2 * w : nullptr;
   const float2* D = NU ? Drow + lane : nullptr;
   unsigned long long evals = 0;   // (line, point) pairs inside the cutoff and the job's window
 
@@ -390,7 +464,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
     const int f16 = Lst.width_f16;
     const float dnu_f = Lst.dnu_f;
     // offsets on a uniform grid round once more (X0 + 32 m dnu), hence the precision margin
-    const float margin_cm = NU ? 0.0f : ROX_FAST_MARGIN * 32.0f * (ROX_K - 1) * dnu_f;
+    const float margin_cm = NU ? 0.0f : fast_margin(dnu_f);
     const int Aw = span * ROX_SPAN;
     const int Bw = Aw + ROX_SPAN - 1;
     if (*Lst.status != ROX_OK) continue;           // list not prepared from sorted lines
@@ -427,8 +501,13 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
       if (plo + lane < phi) {
         const long long li = IDX ? (long long)Lst.idx[plo + lane] : plo + lane;
         cp_async16(&geo_st[0][lane], &Lst.geo[li]);
-        cp_async4(&S_st[0][lane], &S_row[li]);
-        load_widths<BRD>(J, Lst, f16, li, gref, nt);
+        if constexpr (PRE) {
+#pragma unroll
+          for (int c = 0; c < 3; c++) cp_async16(&rec_st[0][lane][c], &Lst.rec[3 * li + c]);
+        } else {
+          cp_async4(&S_st[0][lane], &S_row[li]);
+          load_widths<BRD>(J, Lst, f16, li, gref, nt);
+        }
       }
       if (IDX && plo + 32 + lane < phi) li_n = Lst.idx[plo + 32 + lane];
       cp_async_commit();
@@ -440,8 +519,13 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         if (b0 + 32 + lane < phi) {
           const long long li = IDX ? li_n : b0 + 32 + lane;
           cp_async16(&geo_st[buf ^ 1][lane], &Lst.geo[li]);
-          cp_async4(&S_st[buf ^ 1][lane], &S_row[li]);
-          load_widths<BRD>(J, Lst, f16, li, gref_n, nt_n);
+          if constexpr (PRE) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) cp_async16(&rec_st[buf ^ 1][lane][c], &Lst.rec[3 * li + c]);
+          } else {
+            cp_async4(&S_st[buf ^ 1][lane], &S_row[li]);
+            load_widths<BRD>(J, Lst, f16, li, gref_n, nt_n);
+          }
         }
         if (IDX && b0 + 64 + lane < phi) li_n = Lst.idx[b0 + 64 + lane];
         cp_async_commit();
@@ -455,62 +539,65 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         int jlo = 1, jhi = 0, zlo = 0, zhi = -1;
         if (live) {
           const float4 g = geo_st[buf][lane];
-          const float Sp = S_st[buf][lane];
           jlo = __float_as_int(g.z);
           jhi = __float_as_int(g.w);
-          float nu0f;   // line centre; its offset state {E, F} (uniform grid) or {c hi, c lo} (nodes)
-          if constexpr (NU) {
-            // c = nu0 - (span's first node) as a double-float pair (the hi parts cancel exactly)
-            nu0f = g.x;
-            const float ch = g.x - bh, cl = g.y - bl;
-            ax = ch + cl;
-            ay = cl - (ax - ch);
-          } else {
-            nu0f = Lst.nu_min_f + fmaf(g.x, dnu_f, g.y);
-            ax = (float)Aw - g.x;     // exact: both are integers below 2^24
-            ay = -g.y;
-          }
-          const float gG = nu0f * J.gG_fac;
-          const float gL = BRD ? fmaf(gref, J.p_fac, nt) : gref * rox_exp2(nt * J.l2_ratio) * J.p_fac;
           const int ov = min(jhi, (int)whi) - max(jlo, (int)wlo) + 1;
           if (ov > 0) evals += (unsigned)ov;
-          const float gG2 = gG * gG, gL2 = gL * gL;
-          const float pY = Sp * gL * ROX_INV_PI;
-          const float invG = rox_rcp(gG);
-          yv = gL * invG;
-          const rox_far fc = rox_far_coefs(yv);      // far-zone form of this line (rox_faddeeva.cuh)
-          // slow zone: |X| < sqrt(r2 gamma_G^2 - gamma_L^2), at least the precision margin
-          const float hz2 = fmaxf(0.0f, fc.r2 * gG2 - gL2);
-          float hz = hz2 * rox_rsqrt(hz2);            // 0 for hz2 = 0 (rsqrt(0) = inf, product taken as 0 below)
-          hz = hz2 > 0.0f ? hz : 0.0f;
-          // zone |z| < 6.5 not widened by the margin: the core forms cover all of it
-          const bool core_only = fc.r2 == ROX_S_PADE && hz >= margin_cm;
-          hz = fmaxf(hz, margin_cm);
-          if constexpr (NU) {
-            // the span's offsets run from -c to Ws - c; pass 2 then scans the window itself
-            const float hzp = hz * 1.001f + 1e-6f * (fabsf(ax) + Ws);
-            zoned = -ax < hzp && Ws - ax > -hzp;
-            zlo = jlo;
-            zhi = jhi;
-          } else {
-            // grid indices of the zone, |j - (k0 + f)| < hz / dnu, widened by 1e-4 relative and
-            // one point on each side (covers every point with t < t_z despite the roundings)
-            const int k0 = Aw - (int)ax;
-            const float hzg = fminf(hz * Lst.inv_dnu_f * 1.0001f, 8.0e6f);
-            const float fr = g.y * Lst.inv_dnu_f;
-            zlo = k0 + __float2int_rd(fr - hzg) - 1;
-            zhi = k0 + __float2int_ru(fr + hzg) + 1;
-            zoned = !(Bw < zlo || Aw > zhi);
-          }
           covers = Aw >= jlo && Bw <= jhi;
-          vA = fc.alpha * gG2;
-          vB = fc.beta * (gG2 * gG2);
-          vP = pY;
-          vQ = pY * (fc.kappa * gG2);
-          tz = fmaf(hz, hz, vA);
-          iGs = core_only ? -invG : invG;
-          pcv = Sp * invG * ROX_INV_SQRT_PI;
-          if (zoned) cfv = fmaf(tz, vP, vQ) * rox_rcp(fmaf(tz, tz, vB));
+          LineK kc;
+          if constexpr (PRE) {
+            // uniform grid, constants from k_line_params
+            const float4 r0 = rec_st[buf][lane][0], r1 = rec_st[buf][lane][1], r2 = rec_st[buf][lane][2];
+            kc.A = r0.x;
+            kc.B = r0.y;
+            kc.P = r0.z;
+            kc.Q = r0.w;
+            kc.tz = r1.x;
+            kc.iGs = r1.y;
+            kc.y = r1.z;
+            kc.pc = r1.w;
+            kc.cf = r2.x;
+            zlo = __float_as_int(r2.y);
+            zhi = __float_as_int(r2.z);
+            ax = (float)Aw - g.x;     // exact: both are integers below 2^24
+            ay = -g.y;
+            zoned = !(Bw < zlo || Aw > zhi);
+          } else {
+            const float Sp = S_st[buf][lane];
+            float nu0f;   // line centre; its offset state {E, F} (uniform grid) or {c hi, c lo} (nodes)
+            if constexpr (NU) {
+              // c = nu0 - (span's first node) as a double-float pair (the hi parts cancel exactly)
+              nu0f = g.x;
+              const float ch = g.x - bh, cl = g.y - bl;
+              ax = ch + cl;
+              ay = cl - (ax - ch);
+            } else {
+              nu0f = Lst.nu_min_f + fmaf(g.x, dnu_f, g.y);
+              ax = (float)Aw - g.x;     // exact: both are integers below 2^24
+              ay = -g.y;
+            }
+            kc = line_consts<BRD>(nu0f, Sp, gref, nt, J, margin_cm, false);
+            if constexpr (NU) {
+              // the span's offsets run from -c to Ws - c; pass 2 then scans the window itself
+              const float hzp = kc.hz * 1.001f + 1e-6f * (fabsf(ax) + Ws);
+              zoned = -ax < hzp && Ws - ax > -hzp;
+              zlo = jlo;
+              zhi = jhi;
+            } else {
+              zone_bounds(g, kc.hz, Lst.inv_dnu_f, zlo, zhi);
+              zoned = !(Bw < zlo || Aw > zhi);
+            }
+            if (zoned) kc.cf = fmaf(kc.tz, kc.P, kc.Q) * rox_rcp(fmaf(kc.tz, kc.tz, kc.B));
+          }
+          vA = kc.A;
+          vB = kc.B;
+          vP = kc.P;
+          vQ = kc.Q;
+          tz = kc.tz;
+          iGs = kc.iGs;
+          yv = kc.y;
+          pcv = kc.pc;
+          cfv = kc.cf;
         }
         const unsigned clean = __ballot_sync(0xffffffffu, live && covers && !zoned);
         const unsigned czone = __ballot_sync(0xffffffffu, live && covers && zoned);
@@ -634,6 +721,17 @@ __global__ void k_faddeeva(const float* x, const float* y, float* out, long long
 }  // namespace
 
 #define ROX_NODES_SMEM (ROX_WARPS * ROX_SPAN * sizeof(float2))
+#define ROX_PRE_SMEM (ROX_WARPS * 2 * 32 * 3 * sizeof(float4))
+
+// per-line constants of job J (one (P,T) point) for its lines [J.l0, J.l1): rec[3 i .. 3 i + 2]
+cudaError_t rox_launch_line_params(const RoxListDev& L, const RoxJobDev& J, float4* rec, cudaStream_t s) {
+  const long long n = J.l1 - J.l0;
+  if (n <= 0) return cudaSuccess;
+  long long b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  k_line_params<<<(int)b, 256, 0, s>>>(L, J, rec);
+  return cudaGetLastError();
+}
 
 cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, int extras, cudaStream_t s) {
   if (nodes) {
@@ -649,13 +747,24 @@ cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, in
     k_voigt<false, ROX_VX_INDEX><<<n_blocks, ROX_THREADS, 0, s>>>(A);
   } else if (extras == ROX_VX_BROAD) {
     k_voigt<false, ROX_VX_BROAD><<<n_blocks, ROX_THREADS, 0, s>>>(A);
+  } else if (extras == ROX_VX_PRE) {
+    cudaError_t e = cudaFuncSetAttribute(k_voigt<false, ROX_VX_PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ROX_PRE_SMEM);
+    if (e != cudaSuccess) return e;
+    k_voigt<false, ROX_VX_PRE><<<n_blocks, ROX_THREADS, ROX_PRE_SMEM, s>>>(A);
   } else {
     return cudaErrorNotSupported;   // no entry point combines an indexed list with broadening
   }
   return cudaGetLastError();
 }
 
-cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes) {
+cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes, bool pre) {
+  if (pre) {
+    cudaError_t e = cudaFuncSetAttribute(k_voigt<false, ROX_VX_PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ROX_PRE_SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<false, ROX_VX_PRE>, ROX_THREADS, ROX_PRE_SMEM);
+  }
   if (nodes) {
     cudaError_t e = cudaFuncSetAttribute(k_voigt<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)ROX_NODES_SMEM);

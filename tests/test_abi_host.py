@@ -81,9 +81,12 @@ def test_invalid_arguments_rejected_on_host(lib):
 
 def test_workspace_size_is_host_only(lib):
     G = lib.RoxGrid(300.0, 0.01, 2970001)
-    a = lib.lib.rox_xsec_workspace_size(10_000_000, ctypes.byref(G), 1)
+    one = lib.lib.rox_xsec_workspace_size(10_000_000, ctypes.byref(G), 1)
+    a = lib.lib.rox_xsec_workspace_size(10_000_000, ctypes.byref(G), 2)
     b = lib.lib.rox_xsec_workspace_size(10_000_000, ctypes.byref(G), 20)
-    assert a > 10_000_000 * (16 + 12) and b - a == 19 * 10_000_000 * 12   # FP64 + scaled FP32 strengths
+    assert a > 10_000_000 * (16 + 2 * 12) and b - a == 18 * 10_000_000 * 12   # FP64 + scaled FP32 strengths
+    # one temperature: plus 48 bytes per line of per-line constants, minus one strength row
+    assert one - a == 10_000_000 * (48 - 12)
     assert lib.lib.rox_xsec_workspace_size(10, ctypes.byref(G), 0) == 0
 
 
