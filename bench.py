@@ -610,14 +610,14 @@ def run_gpu(args):
                             " and the nodes" if args.nodes else "", "rox_xsec_nodes_batch" if args.nodes else "rox_xsec",
                             "; two list buffers, step k+1's upload and sort overlap step k's cross-section"
                             if pipelined else "")},
-                "gpu_launches": args.steps * (6 if args.nodes or args.broadening else
-                                              9 if args.select is not None else 5),
+                "gpu_launches": args.steps * 6 if args.select is None else args.steps * 9,
                 "gpu_launches_note": (
                     "per step: windows, strengths, line bins, bin maxima, FP64 fix-up of the bin maxima, "
                     "selection and scaling, kept flags, span ranges over the kept lines, Voigt kernel (+ CUB's "
                     "two select kernels and memsets)" if args.select is not None else
-                    "per step: %swindows, strengths, strength scaling, %stile ranges, Voigt kernel "
-                    "(+ memsets)" % ("node offsets, " if args.nodes else "", "broadening, " if args.broadening else "")),
+                    "per step: %swindows, strengths, strength scaling, %stile ranges, %sVoigt kernel "
+                    "(+ memsets)" % ("node offsets, " if args.nodes else "", "broadening, " if args.broadening else "",
+                                     "" if args.nodes or args.broadening else "per-line constants, ")),
                 "clocks": csum}
         print(json.dumps(line))
     if dist is not None:
@@ -732,7 +732,7 @@ def run_large(args):
             if evs is not None:
                 rox.rox_set_profile_events(*evs[c])
             rox.rox_xsec_batch(L, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws,
-                               flags=rox.ROX_ACCUMULATE if c else 0, stream=stream)
+                               flags=(rox.ROX_ACCUMULATE if c else 0) | rox.ROX_KAHAN, stream=stream)
         if evs is not None:
             rox.rox_set_profile_events(None, None)
 
@@ -740,7 +740,7 @@ def run_large(args):
     evals = 0
     for c, L in enumerate(resident):
         rox.rox_xsec_batch(L, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws,
-                           flags=rox.ROX_ACCUMULATE if c else 0)
+                           flags=(rox.ROX_ACCUMULATE if c else 0) | rox.ROX_KAHAN)
         rc, ev = rox.rox_ws_status(ws)
         if rc != 0:
             raise RuntimeError(rox.lib.rox_last_error().decode())
@@ -817,7 +817,7 @@ def run_large(args):
                 nxt = upload(c + 1) if c + 1 < len(starts) else None
                 main_s.wait_event(up_ev[c % 2])
                 rox.rox_xsec_batch(cur, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws,
-                                   flags=rox.ROX_ACCUMULATE if c else 0)
+                                   flags=(rox.ROX_ACCUMULATE if c else 0) | rox.ROX_KAHAN)
                 comp_ev[c % 2].record(main_s)
                 cur = nxt
             sigma_h.copy_(sigma, non_blocking=True)
@@ -878,14 +878,14 @@ def run_large(args):
                                        "(P,T)=(%g bar, %g K)" % (n, len(starts), w.grid_lo, w.grid_hi, w.dnu, grid[2],
                                                                  w.cutoff, P, T),
                            "evals_per_step": evals, "xsecs_per_s": world * args.steps / (ms * 1e-3),
-                           "step": "rox_xsec_batch per chunk (strengths, widths, windows, span ranges, Voigt "
-                                   "accumulate), chunks after the first with ROX_ACCUMULATE",
+                           "step": "rox_xsec_batch per chunk (strengths, windows, span ranges, per-line constants, "
+                                   "Voigt accumulate), flags ROX_KAHAN, chunks after the first also ROX_ACCUMULATE",
                            "l2": "inputs larger than L2 (line list %.1f GB)" % (line_bytes / 1e9),
                            "sigma_max": sig_max, "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "config2": extra2, "serving": serving,
-                "gpu_launches": args.steps * 5 * len(starts),
-                "gpu_launches_note": "per chunk: windows, strengths, strength scaling, span ranges, Voigt kernel "
-                                     "(+ memsets)",
+                "gpu_launches": args.steps * 6 * len(starts),
+                "gpu_launches_note": "per chunk: windows, strengths, strength scaling, span ranges, per-line "
+                                     "constants, Voigt kernel (+ memsets)",
                 "clocks": csum}
         print(json.dumps(line))
     if dist is not None:
@@ -927,12 +927,20 @@ def config2_summary(args, peaks):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     kms = statistics.mean(a.elapsed_time(b) for a, b in pairs)
+    # the same step with plain (uncompensated) summation of the partial sums
+    t0.record()
+    for _ in range(steps):
+        rox.rox_xsec_batch(lines, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws, flags=0)
+    t1.record()
+    torch.cuda.synchronize()
+    ms_plain = t0.elapsed_time(t1) / steps
     del lines, ws, sigma
     torch.cuda.empty_cache()
     return {"workload": "exomol: %d lines, grid %d points, cutoff %g cm^-1, (P,T)=(%g bar, %g K)" % (
                 w.n_lines, grid[2], w.cutoff, P, T),
             "value": evals / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "status": rc,
-            "kernel_ms": kms, "xsecs_per_s": 1e3 / ms,
+            "kernel_ms": kms, "xsecs_per_s": 1e3 / ms, "summation": "compensated (ROX_KAHAN)",
+            "ms_per_step_plain_sum": ms_plain,
             "roofline_frac": evals * FLOPS_PER_EVAL / (kms * 1e-3) / 1e12 / peaks["formula_tflops"]}
 
 

@@ -46,10 +46,13 @@ extern "C" {
 #define ROX_EINVAL 1      /* invalid argument: null pointer, n <= 0, T <= 0, P < 0, Q <= 0, ... */
 #define ROX_ENOMEM 2      /* workspace smaller than the matching *_workspace_size() */
 #define ROX_ECUDA 3       /* a CUDA runtime call failed (see rox_last_error) */
-#define ROX_ETIMEOUT 4    /* a bounded device-side wait ran out (reported by rox_ws_status) */
+#define ROX_ETIMEOUT 4    /* reserved for a bounded device-side wait running out; no kernel of this
+                             version waits on another, so no call returns it */
 #define ROX_EUNSORTED 5   /* line list not in ascending nu0 (reported by rox_ws_status) */
 #define ROX_ERANGE 6      /* a size beyond a documented limit */
 #define ROX_EGRID 7       /* user-provided nodes not finite or not strictly increasing (rox_ws_status) */
+#define ROX_EOVERFLOW 8   /* a cross-section value beyond the FP32 range (inf or NaN) was written
+                             (rox_ws_status); the other values of the call are valid */
 
 /* line-list conventions */
 #define ROX_HITRAN 0      /* s_or_a = S_ref at 296 K (cm/molecule) */
@@ -59,8 +62,10 @@ extern "C" {
 #define ROX_WIDTH_F32 0
 #define ROX_WIDTH_F16 1
 
-/* flags of rox_xsec_batch */
+/* flags of rox_xsec_batch (and of the rox_job of rox_xsec_jobs) */
 #define ROX_ACCUMULATE 1u /* add into sigma_out instead of overwriting it (chunked line lists) */
+#define ROX_KAHAN 2u      /* compensated (Kahan) summation of the per-batch FP32 partial sums of each
+                             span part; without it they are added plainly (rox_xsec always sets it) */
 
 /* limits */
 #define ROX_MAX_PT 512            /* (P,T) points per rox_xsec_batch call */
@@ -126,6 +131,17 @@ const char* rox_version(void);
 int rox_line_strengths(const rox_lines* lines, double T, double Q_T, double Q_ref,
                        float* S_out, void* stream);
 
+/* a1 -- the strengths exactly as the cross-section launches compute them (rox_xsec_batch and the
+ * calls built on it), in double: the Boltzmann exponent a = -c2 E''(1/T - 1/296) (HITRAN) or
+ * -c2 E''/T (ExoMol) in FP64, reduced as a = k ln2 + r (ln 2 in two parts, Cody and Waite);
+ * exp(r), the stimulated-emission factor(s) and the prefactor in FP32 on a 2^64 pre-scale, put
+ * back by the exact powers 2^-64 and 2^k. Exponents with |a| >= 700 and FP32 products outside
+ * [2^-100, 2^100] take the full FP64 form of rox_line_strengths. Relative error below 1e-6 (the
+ * sum of the FP32 roundings, the expf and expm1f errors included). Paper: "Compute
+ * line-strengths and -widths". Arguments as rox_line_strengths; S_out [n] double (device). */
+int rox_line_strengths_reduced(const rox_lines* lines, double T, double Q_T, double Q_ref,
+                               double* S_out, void* stream);
+
 /* a2 -- Doppler 1/e half-widths gamma_G and Lorentz HWHM gamma_L (cm^-1), FP32 outputs.
  * Paper: "Compute line-strengths and -widths" (pressure broadening: single power law).
  * mass_amu > 0, P_bar >= 0, T > 0. gamma_G_out, gamma_L_out [n] float (device). */
@@ -171,7 +187,7 @@ int rox_faddeeva_re(const float* x, const float* y, float* out, int64_t n, void*
  * P_bar, T, Q_T   [n_pt] HOST arrays: pressure (bar, >= 0), temperature (K, > 0),
  *                 partition function Q(T) (> 0); Q_ref = Q(296 K) (> 0)
  * mass_amu  molecular mass (> 0); cutoff  wing cutoff (cm^-1, > 0), cutoff/dnu <= ROX_MAX_CUTOFF_STEPS
- * flags     0 or ROX_ACCUMULATE
+ * flags     0, ROX_ACCUMULATE, ROX_KAHAN or both
  * sigma_out [n_pt][grid->n] float (device), point-major; each grid point is written once
  *           per call with a fixed summation order (bitwise reproducible run to run).
  * ws        device workspace of rox_xsec_workspace_size(lines->n, grid, n_temps) bytes, where
@@ -187,7 +203,7 @@ int rox_xsec_batch(const rox_lines* lines, const rox_grid* grid, int n_pt,
                    double mass_amu, double cutoff, unsigned flags, float* sigma_out,
                    void* ws, size_t ws_bytes, void* stream);
 
-/* a4 -- one (P,T) point: rox_xsec_batch with n_pt = 1 and flags = 0. */
+/* a4 -- one (P,T) point: rox_xsec_batch with n_pt = 1 and flags = ROX_KAHAN. */
 int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double T,
              double Q_T, double Q_ref, double mass_amu, double cutoff, float* sigma_out,
              void* ws, size_t ws_bytes, void* stream);
@@ -331,7 +347,7 @@ int rox_cia_regrid_nodes(const rox_cia* cia, const rox_nodes* nodes, int n_T, co
 /* Synchronises `stream` and returns the device-side status recorded in `ws` by the last
  * rox_xsec / rox_xsec_batch / rox_xsec_nodes_batch call that used it: ROX_OK, ROX_EUNSORTED
  * (lines not in ascending nu0: no sigma was written), ROX_EGRID (bad nodes: no sigma was
- * written), or ROX_ETIMEOUT. If evals_out is not NULL it
+ * written), or ROX_EOVERFLOW (some sigma value is not finite in FP32). If evals_out is not NULL it
  * receives the number of (line, grid point) pairs inside the cutoff summed over the
  * call's (P,T) points (the unit of work of the Voigt kernel). */
 int rox_ws_status(const void* ws, unsigned long long* evals_out, void* stream);
@@ -362,7 +378,7 @@ int rox_prepare(const rox_lines* lines, const rox_grid* lattice, double cutoff, 
  * span_hi[(first + n - 1) / ROX_SPAN] - line_first; lines outside the range are skipped. */
 typedef struct rox_job {
   int32_t list;               /* index into the `lists` of rox_xsec_jobs */
-  uint32_t flags;             /* 0 or ROX_ACCUMULATE */
+  uint32_t flags;             /* 0, ROX_ACCUMULATE, ROX_KAHAN or both */
   int64_t first, n;           /* lattice points [first, first + n) */
   int64_t line_first, line_count;
   double P_bar, T, Q_T, Q_ref, mass_amu;

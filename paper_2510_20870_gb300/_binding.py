@@ -13,10 +13,11 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librox.so")
 
-ROX_OK, ROX_EINVAL, ROX_ENOMEM, ROX_ECUDA, ROX_ETIMEOUT, ROX_EUNSORTED, ROX_ERANGE, ROX_EGRID = range(8)
+ROX_OK, ROX_EINVAL, ROX_ENOMEM, ROX_ECUDA, ROX_ETIMEOUT, ROX_EUNSORTED, ROX_ERANGE, ROX_EGRID, ROX_EOVERFLOW = range(9)
 ROX_HITRAN, ROX_EXOMOL = 0, 1
 ROX_WIDTH_F32, ROX_WIDTH_F16 = 0, 1
 ROX_ACCUMULATE = 1
+ROX_KAHAN = 2
 ROX_MAX_PT = 512
 ROX_TILE = 256  # grid points per Voigt work item (one warp: 32 lanes x ROX_K points)
 
@@ -89,6 +90,7 @@ def _load():
         "rox_version": (ctypes.c_char_p, []),
         "rox_line_strengths": (ctypes.c_int, [P, D, D, D, P, P]),
         "rox_line_widths": (ctypes.c_int, [P, D, D, D, P, P, P]),
+        "rox_line_strengths_reduced": (ctypes.c_int, [P, D, D, D, P, P]),
         "rox_sort_workspace_size": (ctypes.c_size_t, [I64]),
         "rox_sort_lines": (ctypes.c_int, [P, P, P, P, ctypes.c_size_t, P]),
         "rox_line_windows": (ctypes.c_int, [P, I64, P, D, P, P, P, P, P, P, P]),
@@ -176,6 +178,12 @@ def grid_struct(grid):
 def rox_line_strengths(lines, T, Q_T, Q_ref, S_out, stream=None):
     L = lines_struct(lines)
     _check(lib.rox_line_strengths(ctypes.byref(L), T, Q_T, Q_ref, _ptr(S_out), _stream(stream)))
+
+
+def rox_line_strengths_reduced(lines, T, Q_T, Q_ref, S_out, stream=None):
+    """S(T) as the cross-section launches compute it (reduced form), float64 CUDA tensor S_out."""
+    L = lines_struct(lines)
+    _check(lib.rox_line_strengths_reduced(ctypes.byref(L), T, Q_T, Q_ref, _ptr(S_out), _stream(stream)))
 
 
 def rox_line_widths(lines, mass_amu, P_bar, T, gamma_G_out, gamma_L_out, stream=None):

@@ -12,6 +12,8 @@
 // kernels (rox_params.cu, rox_geometry.cu, rox_voigt.cu)
 cudaError_t rox_launch_strengths(const rox_lines* L, double T, double Q_T, double Q_ref, float* S_out,
                                  cudaStream_t s);
+cudaError_t rox_launch_strengths_reduced(const rox_lines* L, double T, double Q_T, double Q_ref, double* S_out,
+                                         cudaStream_t s);
 cudaError_t rox_launch_widths(const rox_lines* L, double mass_amu, double P_bar, double T, float* gG,
                               float* gL, cudaStream_t s);
 cudaError_t rox_launch_strengths_multi(const rox_lines* L, int n_temps, const double* temps,
@@ -378,6 +380,18 @@ int rox_line_strengths(const rox_lines* lines, double T, double Q_T, double Q_re
   return rc ? rc : ok();
 }
 
+int rox_line_strengths_reduced(const rox_lines* lines, double T, double Q_T, double Q_ref, double* S_out,
+                               void* stream) {
+  int rc = check_lines(lines, true, false);
+  if (rc) return rc;
+  if (!finite_pos(T) || !finite_pos(Q_T) || !finite_pos(Q_ref)) return fail(ROX_EINVAL, "T, Q_T, Q_ref must be > 0");
+  if (lines->n > 0 && !S_out) return fail(ROX_EINVAL, "S_out is NULL");
+  if (lines->n == 0) return ok();
+  rc = cuda_check(rox_launch_strengths_reduced(lines, T, Q_T, Q_ref, S_out, (cudaStream_t)stream),
+                  "strengths kernel");
+  return rc ? rc : ok();
+}
+
 int rox_line_widths(const rox_lines* lines, double mass_amu, double P_bar, double T, float* gamma_G_out,
                     float* gamma_L_out, void* stream) {
   int rc = check_lines(lines, false, true);
@@ -465,7 +479,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   if (n_pt < 1 || n_pt > ROX_MAX_PT) return fail(ROX_EINVAL, "n_pt = %d outside [1, %d]", n_pt, ROX_MAX_PT);
   if (!P_bar || !T || !Q_T) return fail(ROX_EINVAL, "P_bar, T, Q_T host arrays required");
   if (!finite_pos(Q_ref) || !finite_pos(mass_amu)) return fail(ROX_EINVAL, "Q_ref and mass must be > 0");
-  if (flags & ~ROX_ACCUMULATE) return fail(ROX_EINVAL, "unknown flags 0x%x", flags);
+  if (flags & ~(ROX_ACCUMULATE | ROX_KAHAN)) return fail(ROX_EINVAL, "unknown flags 0x%x", flags);
   if (!sigma_out) return fail(ROX_EINVAL, "sigma_out is NULL");
   // distinct temperatures (S(T) is computed once per temperature)
   std::vector<double> temps, qs;
@@ -753,7 +767,7 @@ int rox_xsec_tail(const rox_lines* lines, const rox_grid* grid, double P_bar, do
   int rc;
   if ((rc = check_grid(grid))) return rc;
   if ((rc = check_cutoff(cutoff, grid))) return rc;
-  return xsec_batch_impl(lines, grid, nullptr, 1, &P_bar, &T, &Q_T, Q_ref, mass_amu, cutoff, 0u, sigma_out, ws,
+  return xsec_batch_impl(lines, grid, nullptr, 1, &P_bar, &T, &Q_T, Q_ref, mass_amu, cutoff, ROX_KAHAN, sigma_out, ws,
                          ws_bytes, stream, nullptr, nullptr, tail_max, false);
 }
 
@@ -761,7 +775,7 @@ extern "C" {
 
 int rox_xsec(const rox_lines* lines, const rox_grid* grid, double P_bar, double T, double Q_T, double Q_ref,
              double mass_amu, double cutoff, float* sigma_out, void* ws, size_t ws_bytes, void* stream) {
-  return rox_xsec_batch(lines, grid, 1, &P_bar, &T, &Q_T, Q_ref, mass_amu, cutoff, 0u, sigma_out, ws, ws_bytes,
+  return rox_xsec_batch(lines, grid, 1, &P_bar, &T, &Q_T, Q_ref, mass_amu, cutoff, ROX_KAHAN, sigma_out, ws, ws_bytes,
                         stream);
 }
 
@@ -883,7 +897,7 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     if (!finite_pos(j.T) || !finite_pos(j.Q_T) || !finite_pos(j.Q_ref) || !finite_pos(j.mass_amu) ||
         !std::isfinite(j.P_bar) || j.P_bar < 0)
       return fail(ROX_EINVAL, "job %d: T, Q_T, Q_ref, mass > 0 and P >= 0 required", k);
-    if (j.flags & ~ROX_ACCUMULATE) return fail(ROX_EINVAL, "job %d: unknown flags", k);
+    if (j.flags & ~(ROX_ACCUMULATE | ROX_KAHAN)) return fail(ROX_EINVAL, "job %d: unknown flags", k);
     if (!j.sigma_out) return fail(ROX_EINVAL, "job %d: sigma_out is NULL", k);
   }
   if (!ws || ((uintptr_t)ws & 255)) return fail(ROX_EINVAL, "workspace NULL or not 256-byte aligned");
@@ -993,8 +1007,8 @@ int rox_ws_status(const void* ws, unsigned long long* evals_out, void* stream) {
   if (rc) return rc;
   if (evals_out) *evals_out = h.evals_total;
   if (h.status == ROX_EUNSORTED) return fail(ROX_EUNSORTED, "line list is not sorted by ascending nu0");
-  if (h.status == ROX_ETIMEOUT) return fail(ROX_ETIMEOUT, "a device-side wait ran out");
   if (h.status != ROX_OK) return fail(h.status, "device status %d", h.status);
+  if (h.overflow) return fail(ROX_EOVERFLOW, "a cross-section value is beyond the FP32 range");
   return ok();
 }
 

@@ -32,12 +32,12 @@
 
 // Workspace header at the start of every xsec / prepared-list workspace.
 struct RoxWsHeader {
-  int32_t status;                  // ROX_OK / ROX_EUNSORTED / ROX_ETIMEOUT
+  int32_t status;                  // ROX_OK / ROX_EUNSORTED / ROX_EGRID
   int32_t n_pt;
   unsigned long long evals_lines;  // (line, point) pairs inside the cutoff on the whole lattice
   unsigned long long evals_total;  // pairs evaluated by the last Voigt launch(es), all jobs
   int32_t work_counter;            // persistent-kernel work queue
-  int32_t pad;
+  int32_t overflow;                // set by the Voigt kernel when it writes a non-finite sigma
   unsigned long long smax_bits[ROX_MAX_PT];  // per strength row: max S (double bits)
 };
 #define ROX_WS_HEADER_BYTES 8192
@@ -113,7 +113,7 @@ struct RoxJobDev {
   float p_fac;      // P / P_ref
   float gG_fac;     // sqrt(2 k T / (m amu)) / c  -> gamma_G = nu0 * gG_fac
   float l2_ratio;   // log2(T_ref / T)           -> (T_ref/T)^n_T = exp2(n_T * l2_ratio)
-  uint32_t flags;   // ROX_ACCUMULATE
+  uint32_t flags;   // ROX_ACCUMULATE, ROX_KAHAN
   int32_t t_row;    // broadened lists: the job's temperature row of the list's gLT
 };
 

@@ -79,6 +79,15 @@ __global__ void k_strengths(rox_lines L, StrengthConsts k, float* S_out) {
   }
 }
 
+// the reduced form alone, in double (rox_line_strengths_reduced: what the cross-section launches use)
+__global__ void k_strengths_reduced(rox_lines L, StrengthConsts k, double* S_out) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += stride) {
+    const float g = (L.convention == ROX_EXOMOL) ? L.g_up[i] : 1.0f;
+    S_out[i] = line_strength_fast(k, L.nu0[i], L.s_or_a[i], g, L.e_lower[i]);
+  }
+}
+
 __global__ void k_widths(rox_lines L, double gG_fac, float l2_ratio, float p_fac,
                          float* gG_out, float* gL_out) {
   long long stride = (long long)gridDim.x * blockDim.x;
@@ -362,6 +371,12 @@ int grid_for(long long n) {
 cudaError_t rox_launch_strengths(const rox_lines* L, double T, double Q_T, double Q_ref,
                                  float* S_out, cudaStream_t s) {
   k_strengths<<<grid_for(L->n), 256, 0, s>>>(*L, make_consts(L->convention, T, Q_T, Q_ref), S_out);
+  return cudaGetLastError();
+}
+
+cudaError_t rox_launch_strengths_reduced(const rox_lines* L, double T, double Q_T, double Q_ref, double* S_out,
+                                         cudaStream_t s) {
+  k_strengths_reduced<<<grid_for(L->n), 256, 0, s>>>(*L, make_consts(L->convention, T, Q_T, Q_ref), S_out);
   return cudaGetLastError();
 }
 

@@ -462,6 +462,7 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
     const int local = item - (k > 0 ? A.item_end[k - 1] : 0);
     const int span = J.span_first + J.n_spans - 1 - local;       // wide-line (high nu) spans first
     const int f16 = Lst.width_f16;
+    const bool kahan = (J.flags & ROX_KAHAN) != 0;
     const float dnu_f = Lst.dnu_f;
     // offsets on a uniform grid round once more (X0 + 32 m dnu), hence the precision margin
     const float margin_cm = NU ? 0.0f : fast_margin(dnu_f);
@@ -645,26 +646,40 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         for (unsigned z = zslots; z; z &= z - 1)
           zone_line<NU>(PT, LT, __ffs(z) - 1, Aw, lane, lanef, dnu_f, Lst.inv_dnu_f, s_daw, D, zacc);
         __syncwarp();
-        // compensated (Kahan) accumulation of the partial sums, every 4 batches
+        // the partial sums into the part's total every 4 batches: compensated (Kahan) with
+        // ROX_KAHAN, else plainly
         if ((nb & 3) == 3 || b0 + 32 >= phi) {
+          if (kahan) {
 #pragma unroll
-          for (int m = 0; m < ROX_K; m++) {
-            const float yk = acc[m] - cmp[m];
-            const float tk = tot[m] + yk;
-            cmp[m] = (tk - tot[m]) - yk;
-            tot[m] = tk;
-            acc[m] = 0.f;
+            for (int m = 0; m < ROX_K; m++) {
+              const float yk = acc[m] - cmp[m];
+              const float tk = tot[m] + yk;
+              cmp[m] = (tk - tot[m]) - yk;
+              tot[m] = tk;
+              acc[m] = 0.f;
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < ROX_K; m++) {
+              tot[m] += acc[m];
+              acc[m] = 0.f;
+            }
           }
         }
       }
       cp_async_wait0();
       // fold in the pass-2 (near-centre) sums
+      if (kahan) {
 #pragma unroll
-      for (int m = 0; m < ROX_K; m++) {
-        const float yk = zacc[32 * m + lane] - cmp[m];
-        const float tk = tot[m] + yk;
-        cmp[m] = (tk - tot[m]) - yk;
-        tot[m] = tk;
+        for (int m = 0; m < ROX_K; m++) {
+          const float yk = zacc[32 * m + lane] - cmp[m];
+          const float tk = tot[m] + yk;
+          cmp[m] = (tk - tot[m]) - yk;
+          tot[m] = tk;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < ROX_K; m++) tot[m] += zacc[32 * m + lane];
       }
       if (part >= 0) {           // a split item: this part's sum goes to the tail scratch
         float* dst = A.tail_part + ((size_t)(item - A.n_whole) * ROX_PARTS + p) * ROX_SPAN;
@@ -695,16 +710,21 @@ __global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant_
         stot[32 * m + lane] = v;
       }
     }
-    // ---- write the span once (its part inside the job's window)
+    // ---- write the span once (its part inside the job's window); a value beyond the FP32
+    // range is written as it is and flagged (rox_ws_status: ROX_EOVERFLOW)
     float* out = J.sigma - J.first;
+    bool bad = false;
 #pragma unroll
     for (int m = 0; m < ROX_K; m++) {
       const long long j = (long long)Aw + 32 * m + lane;
       if (j >= wlo && j <= whi) {
         const float v = ldexpf(stot[32 * m + lane], e);
-        out[j] = (J.flags & ROX_ACCUMULATE) ? out[j] + v : v;
+        const float o = (J.flags & ROX_ACCUMULATE) ? out[j] + v : v;
+        bad |= !isfinite(o);
+        out[j] = o;
       }
     }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&A.hdr->overflow, 1);
     __syncwarp();
   }
 #pragma unroll

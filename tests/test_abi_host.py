@@ -77,6 +77,12 @@ def test_invalid_arguments_rejected_on_host(lib):
     # cutoff
     assert L.rox_xsec(ctypes.byref(lines), ctypes.byref(G), 1.0, 1000.0, 1.0, 1.0, 18.0, 0.0, 8, 256, 1 << 30,
                       None) == lib.ROX_EINVAL
+    # flags: ROX_ACCUMULATE | ROX_KAHAN are the only ones (an unknown bit is refused before any launch)
+    one = (ctypes.c_double * 1)
+    for bad in (4, 8, 0x100):
+        rc = L.rox_xsec_batch(ctypes.byref(lines), ctypes.byref(G), 1, one(1.0), one(1000.0), one(1.0), 1.0, 18.0,
+                              25.0, bad, 8, 256, 1 << 30, None)
+        assert rc == lib.ROX_EINVAL and b"flags" in L.rox_last_error(), bad
 
 
 def test_workspace_size_is_host_only(lib):

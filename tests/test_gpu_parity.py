@@ -153,15 +153,36 @@ def test_device_faddeeva_matches_wofz():
 
 # ------------------------------------------------------------------ a4: full cross-sections
 def test_config1_full_vs_oracle():
+    """Config 1 over its whole grid, with plain and with compensated (ROX_KAHAN) summation of the
+    partial sums; M is the oracle's own maximum."""
     w = rs.CONFIGS[1]
     L = oracle.sort_lines(rs.make_lines(w))
     grid = rs.grid_of(w)
     (P, T), = w.pts
     Qt, Qr = q_pair(w, T)
     ref = oracle.xsec_windowed(L, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff)
-    sig, evals = _run_xsec(to_device(L, torch), grid, [(P, T, Qt)], Qr, w.mass_amu, w.cutoff)
-    check_sigma(sig[0], ref, label="config 1")
-    assert evals == oracle.count_evals(L["nu0"], *grid, w.cutoff)
+    dl = to_device(L, torch)
+    for flags, label in ((0, "plain sum"), (rox.ROX_KAHAN, "compensated sum")):
+        sig, evals = _run_xsec(dl, grid, [(P, T, Qt)], Qr, w.mass_amu, w.cutoff, flags=flags)
+        check_sigma(sig[0], ref, label="config 1, " + label)
+        assert evals == oracle.count_evals(L["nu0"], *grid, w.cutoff)
+
+
+def test_overflow_is_reported():
+    """A cross-section beyond the FP32 range (S_ref near FLT_MAX) is written as inf and the call's
+    status is ROX_EOVERFLOW; a normal call on the same workspace afterwards reports ROX_OK."""
+    w, L = _small_lines(0, 200, 1000.0, 1010.0, 5)
+    grid = (1000.0, 0.01, 1001)
+    Qt, Qr = q_pair(w, 296.0)
+    big = dict(L)
+    big["s_or_a"] = np.full(len(L["nu0"]), 3.0e38, dtype=np.float32)
+    ws = torch.empty(rox.rox_xsec_workspace_size(len(L["nu0"]), grid, 1), dtype=torch.uint8, device="cuda")
+    sigma = torch.empty((1, grid[2]), dtype=torch.float32, device="cuda")
+    rox.rox_xsec(to_device(big, torch), grid, 1.0, 296.0, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
+    rc, _ = rox.rox_ws_status(ws)
+    assert rc == rox.ROX_EOVERFLOW and not torch.isfinite(sigma).all()
+    rox.rox_xsec(to_device(L, torch), grid, 1.0, 296.0, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws)
+    assert rox.rox_ws_status(ws)[0] == 0 and torch.isfinite(sigma).all()
 
 
 @pytest.mark.parametrize("case", ["ragged", "pure_doppler", "lorentz_dominated", "narrow_undersampled",
@@ -249,11 +270,13 @@ def test_config2_full_size_sampled_windows():
     sig, evals = _run_xsec(out, grid, [(P, T, Qt)], Qr, w.mass_amu, w.cutoff)
     assert evals == oracle.count_evals(Ls["nu0"], *grid, w.cutoff)
     rng = np.random.default_rng(2)
-    starts = [0, grid[2] - 96] + list(rng.integers(0, grid[2] - 96, 8))
+    starts = [0, grid[2] - 96] + list(rng.integers(0, grid[2] - 96, 48))
     M = float(sig[0].max())   # the oracle's max is not available at full size; GPU max stands in (1e-4 close)
+    worst = 0.0
     for s in starts:
         ref = oracle.xsec_window(Ls, grid, int(s), int(s) + 96, P, T, Qt, Qr, w.mass_amu, w.cutoff)
-        check_sigma(sig[0, s:s + 96], ref, M=M, label="window %d" % s)
+        worst = max(worst, check_sigma(sig[0, s:s + 96], ref, M=M, label="window %d" % s))
+    print("PARITY exomol full size, %d windows: worst %.3e" % (len(starts), worst))
 
 
 # ------------------------------------------------------------------ a4 for many requests (serving path)

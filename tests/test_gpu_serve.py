@@ -36,6 +36,14 @@ def server():
     return serve.Server(lists, LATTICE, w0.cutoff, w0.mass_amu, rs.q_table(w0), max_inflight=3, max_batch=16)
 
 
+def _lines_near(w, lo, hi):
+    """Host-generated, nu0-sorted lines of list w with nu0 in [lo, hi] (scanned chunk by chunk)."""
+    found = []
+    for start, nu0 in rs.nu0_in_chunks(w):
+        found.append(start + np.nonzero((nu0 >= lo) & (nu0 <= hi))[0])
+    return oracle.sort_lines(rs.make_lines_at(w, np.concatenate(found)))
+
+
 def test_results_alone_equal_results_in_the_mix(server):
     reqs = serve.requests_from_stream(rs.serve_requests(400.0, 40, seed=11), LATTICE)
     mixed = server.run(reqs, realtime=True)
@@ -46,6 +54,22 @@ def test_results_alone_equal_results_in_the_mix(server):
         assert np.array_equal(alone.sigma, m.sigma), r.rid
     stats = serve.latency_stats(mixed)
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    # the oracle on 3 of the 40 served requests (7.5%), one per list of 1e6, 1e7 and 1e8 lines,
+    # on 64 points in the middle of each window
+    w0 = rs.SERVE_LISTS[0]
+    Qr = q_pair(w0, 296.0)[1]
+    nu_min, dnu, _ = LATTICE
+    for lid in (1, 2, 3):
+        k = next(i for i, r in enumerate(reqs) if r.list_id == lid)
+        r, m = reqs[k], mixed[k]
+        s0 = r.first + max(0, r.n // 2 - 32)
+        n = min(64, r.n)
+        w = rs.SERVE_LISTS[lid]
+        L = _lines_near(w, nu_min + dnu * s0 - w.cutoff - 0.05, nu_min + dnu * (s0 + n - 1) + w.cutoff + 0.05)
+        Qt = q_pair(w, r.t_k)[0]
+        ref = oracle.xsec_window(L, LATTICE, s0, s0 + n, r.p_bar, r.t_k, Qt, Qr, w.mass_amu, w.cutoff)
+        check_sigma(m.sigma[s0 - r.first:s0 - r.first + n], ref, M=float(m.sigma.max()),
+                    label="served request %d (list %d)" % (r.rid, lid))
 
 
 def test_served_windows_match_the_oracle(server):

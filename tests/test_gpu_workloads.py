@@ -67,12 +67,15 @@ def test_device_generator_matches_host(cid, start, count):
 
 
 @pytest.mark.slow
-def test_batch_1e8_lines_points_in_one_launch(pool):
+def test_batch_1e8_lines_all_300_points_in_one_launch(pool):
+    """The batch workload at full size: 1e8 lines, all 15 P x 20 T points in one call (the
+    low-pressure, low-temperature corner, where gamma_G ~ 6e-4 cm^-1 lies below the 0.01 cm^-1
+    step, included), checked on 8 windows of 32 points (both grid ends and six drawn at random)
+    at every point. M is the GPU's own maximum of each cross-section (the oracle cannot sum
+    1e8 lines over 2,970,001 points here), which the windows show to be within the tolerance."""
     w = rs.CONFIGS[3]
     grid = rs.grid_of(w)
-    pts_all = rs.pt_points(w)                    # 15 P x 20 T, P-major
-    pick = [(p, t) for p in (0, 7, 14) for t in (0, 10, 19)]
-    pts = [pts_all[p * 20 + t] for p, t in pick]
+    pts = rs.pt_points(w)                        # 15 P x 20 T, P-major
     Qr = q_pair(w, 296.0)[1]
     dl = _sorted_device(w, w.n_lines)
     n_temps = len(set(T for _, T in pts))
@@ -81,19 +84,27 @@ def test_batch_1e8_lines_points_in_one_launch(pool):
     Qts = [q_pair(w, T)[0] for _, T in pts]
     rox.rox_xsec_batch(dl, grid, [P for P, _ in pts], [T for _, T in pts], Qts, Qr, w.mass_amu, w.cutoff, sigma, ws)
     rc, evals = rox.rox_ws_status(ws)
-    assert rc == 0 and evals > 4e12
-    sig = sigma.cpu().numpy()
-    del dl, ws, sigma
-    windows = [(0, 48), (1_234_567, 1_234_615), (grid[2] - 48, grid[2])]
+    assert rc == 0 and evals > 1e14
+    del dl, ws
+    rng = np.random.default_rng(3)
+    width = 32
+    starts = [0, grid[2] - width] + [int(x) for x in rng.integers(0, grid[2] - width, 6)]
+    windows = [(a, a + width) for a in starts]
+    sig = np.stack([sigma[:, a:b].cpu().numpy() for a, b in windows], axis=1)   # [pt][window][point]
+    M = sigma.max(dim=1).values.double().cpu().numpy()
+    del sigma
     wl = _window_lines(w, windows, grid, w.cutoff)
     tasks, where = [], []
     for k, (P, T) in enumerate(pts):
         for q, (a, b) in enumerate(windows):
             tasks.append((wl[q], grid, a, b, P, T, Qts[k], Qr, w.mass_amu, w.cutoff))
-            where.append((k, a, b))
-    refs = pool.map(_oracle_window, tasks, chunksize=1)
-    for (k, a, b), ref in zip(where, refs):
-        check_sigma(sig[k, a:b], ref, M=float(sig[k].max()), label="P=%g T=%g [%d,%d)" % (pts[k] + (a, b)))
+            where.append((k, q))
+    refs = pool.map(_oracle_window, tasks, chunksize=4)
+    worst = 0.0
+    for (k, q), ref in zip(where, refs):
+        worst = max(worst, check_sigma(sig[k, q], ref, M=float(M[k]),
+                                       label="P=%g T=%g [%d,%d)" % (pts[k] + windows[q])))
+    print("PARITY batch 300 points x 8 windows: worst %.3e" % worst)
 
 
 @pytest.mark.slow
