@@ -80,6 +80,9 @@ def parse():
                          "same wavenumber range (rox_xsec_nodes_batch)" % rs.FIXED_R)
     ap.add_argument("--serve-rates", default="50,100,200,500", help="Poisson request rates (req/s) of the serving leg")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window per rate (s)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="sweep the Voigt launch configuration (paper_2510_20870_gb300/autotune.py) on the large "
+                         "list's 1e8-line chunk and on the exomol list, write the cache and print the results")
     return ap.parse_args()
 
 
@@ -353,6 +356,8 @@ def run_gpu(args):
 
     w, grid, P, T, q = workload(args.config)
     Qt, Qr = q_of(q, T), q_of(q, 296.0)
+    from paper_2510_20870_gb300 import autotune
+    launch_cfg, tuned = autotune.apply("exomol" if args.config == 2 else w.name)
     host = rs.make_lines(w, 0, args.lines)     # unsorted, generation order
     cols = ["nu0", "s_or_a", "g_up", "e_lower", "gamma_ref", "n_t"]
     pinned = {k: torch.from_numpy(host[k]).pin_memory() for k in cols if host[k] is not None}
@@ -601,7 +606,8 @@ def run_gpu(args):
                                    "ranges, Voigt accumulate); the once-per-list sort is inside e2e",
                            "l2": "inputs larger than L2 (line list %.0f MB, workspace %.0f MB)" % (
                                h2d_bytes / 1e6, ws_mb),
-                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "launch_config": launch_cfg, "launch_config_tuned": tuned},
                 "roofline": roof, "cpu_baseline": cpu, "serving": serving,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
                         "d2h_bytes_per_step": sigma_bytes,
@@ -726,6 +732,8 @@ def run_large(args):
     line_bytes = sum(v.numel() * v.element_size() for L in resident for k, v in L.items() if k in cols)
     ws = torch.empty(rox.rox_xsec_workspace_size(chunk, grid, 1), dtype=torch.uint8, device=dev)
     sigma = torch.empty((1, grid[2]), dtype=torch.float32, device=dev)
+    from paper_2510_20870_gb300 import autotune
+    launch_cfg, tuned = autotune.apply("large")
 
     def step(evs=None, lines=resident, stream=None):
         for c, L in enumerate(lines):
@@ -881,7 +889,10 @@ def run_large(args):
                            "step": "rox_xsec_batch per chunk (strengths, windows, span ranges, per-line constants, "
                                    "Voigt accumulate), flags ROX_KAHAN, chunks after the first also ROX_ACCUMULATE",
                            "l2": "inputs larger than L2 (line list %.1f GB)" % (line_bytes / 1e9),
-                           "sigma_max": sig_max, "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "sigma_max": sig_max, "parallelism": "replicas" if world > 1 else "single GPU",
+                           "launch_config": launch_cfg,
+                           "launch_config_source": "autotuner cache (paper_2510_20870_gb300/tuning.json)" if tuned
+                                                   else "library default (no cache entry for this GPU)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "config2": extra2, "serving": serving,
                 "gpu_launches": args.steps * 6 * len(starts),
                 "gpu_launches_note": "per chunk: windows, strengths, strength scaling, span ranges, per-line "
@@ -898,8 +909,10 @@ def config2_summary(args, peaks):
     import torch
     import paper_2510_20870_gb300 as rox
     from rox_synth.device import make_lines_device
+    from paper_2510_20870_gb300 import autotune
     w, grid, P, T, q = workload(2)
     Qt, Qr = q_of(q, T), q_of(q, 296.0)
+    launch_cfg, tuned = autotune.apply("exomol")
     raw = make_lines_device(w, 0, w.n_lines)
     lines = {k: (torch.empty_like(v) if isinstance(v, torch.Tensor) else v) for k, v in raw.items()}
     sws = torch.empty(rox.rox_sort_workspace_size(w.n_lines), dtype=torch.uint8, device="cuda")
@@ -940,7 +953,7 @@ def config2_summary(args, peaks):
                 w.n_lines, grid[2], w.cutoff, P, T),
             "value": evals / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "status": rc,
             "kernel_ms": kms, "xsecs_per_s": 1e3 / ms, "summation": "compensated (ROX_KAHAN)",
-            "ms_per_step_plain_sum": ms_plain,
+            "ms_per_step_plain_sum": ms_plain, "launch_config": launch_cfg, "launch_config_tuned": tuned,
             "roofline_frac": evals * FLOPS_PER_EVAL / (kms * 1e-3) / 1e12 / peaks["formula_tflops"]}
 
 
@@ -1082,8 +1095,44 @@ def run_cia(args):
                       "gpu_launches": 2 * args.steps, "clocks": clocks.summary(), "cpu_baseline": cpu, "e2e": e2e}))
 
 
+def run_autotune(args):
+    """Sweeps the launch configuration on one 1e8-line chunk of the large list and on the exomol
+    list, writes the cache (paper_2510_20870_gb300/tuning.json) and prints the results."""
+    import torch
+    import paper_2510_20870_gb300 as rox
+    from paper_2510_20870_gb300 import autotune
+    from rox_synth.device import make_lines_device
+    out = {}
+    for cls, cid, n in (("large", 4, 100_000_000), ("exomol", 2, None)):
+        w = rs.CONFIGS[cid]
+        grid = rs.grid_of(w)
+        (P, T), = w.pts
+        q = rs.q_table(w)
+        Qt, Qr = q_of(q, T), q_of(q, 296.0)
+        n = n or w.n_lines
+        raw = make_lines_device(w, 0, n)
+        lines = {k: (torch.empty_like(v) if isinstance(v, torch.Tensor) else v) for k, v in raw.items()}
+        sws = torch.empty(rox.rox_sort_workspace_size(n), dtype=torch.uint8, device="cuda")
+        rox.rox_sort_lines(raw, lines, None, sws)
+        del raw, sws
+        ws = torch.empty(rox.rox_xsec_workspace_size(n, grid, 1), dtype=torch.uint8, device="cuda")
+        sigma = torch.empty((1, grid[2]), dtype=torch.float32, device="cuda")
+
+        def step():
+            rox.rox_xsec_batch(lines, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws, flags=rox.ROX_KAHAN)
+        res = autotune.sweep(step, reps=2 if cid == 4 else 5)
+        best = autotune.save(cls, res, note="%s: %d lines, one rox_xsec_batch call" % (w.name, n))
+        out[autotune.key(cls)] = {"best": best, "results": [{"config": c, "ms": ms} for c, ms in res]}
+        del lines, ws, sigma
+        torch.cuda.empty_cache()
+    print(json.dumps({"autotune": out, "cache": autotune.CACHE}))
+
+
 def main():
     args = parse()
+    if args.autotune:
+        run_autotune(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.cia:

@@ -401,6 +401,25 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
  * stream. Pass NULL, NULL to stop. Recording is stream-ordered and adds no sync. */
 int rox_set_profile_events(void* start, void* stop);
 
+/* Launch configuration of the Voigt kernel, process-wide (the paper has no counterpart; it is a
+ * tuning knob of this library, chosen by the autotuner, paper_2510_20870_gb300/autotune.py):
+ *   warps_per_cta  4 or 8 (default 8)
+ *   ctas_per_sm    CTAs per SM of the persistent grid, 1..the kernel's resident maximum; 0 (default)
+ *                  or a larger value: the maximum
+ *   split_rounds   1..4 (default 1): after the whole work items, this many rounds of the launch's
+ *                  warps worth of items are split into parts, so the launch ends in small pieces
+ * No setting changes any result: the summation order of every span is fixed whatever the launch.
+ * rox_set_launch_config(NULL) restores the defaults; out-of-range values return ROX_EINVAL and
+ * change nothing. Takes effect for the calls that start after it (thread-safe). */
+typedef struct rox_launch_config {
+  int32_t warps_per_cta;
+  int32_t ctas_per_sm;
+  int32_t split_rounds;
+  int32_t pad;
+} rox_launch_config;
+int rox_set_launch_config(const rox_launch_config* cfg);
+int rox_get_launch_config(rox_launch_config* out);
+
 /* Measurement helper (the paper has no counterpart): the FP32 fused multiply-add rate of this
  * GPU, the denominator of the Voigt kernel's roofline. Launches n_blocks blocks of 256 threads,
  * each thread running 16 independent FMA chains for reps x 8 rounds; out is a DEVICE buffer of

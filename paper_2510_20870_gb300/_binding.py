@@ -72,6 +72,11 @@ class RoxPrepared(ctypes.Structure):
                 ("span_lo", ctypes.c_void_p), ("span_hi", ctypes.c_void_p), ("n_spans", ctypes.c_int64)]
 
 
+class RoxLaunchConfig(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("split_rounds", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
 class RoxJob(ctypes.Structure):
     _fields_ = [("list", ctypes.c_int32), ("flags", ctypes.c_uint32), ("first", ctypes.c_int64), ("n", ctypes.c_int64),
                 ("line_first", ctypes.c_int64), ("line_count", ctypes.c_int64), ("P_bar", ctypes.c_double),
@@ -119,6 +124,8 @@ def _load():
         "rox_cia_regrid_nodes": (ctypes.c_int, [P, P, ctypes.c_int, P, P, P]),
         "rox_xsec_broadened_workspace_size": (ctypes.c_size_t, [I64, P, ctypes.c_int]),
         "rox_fp32_probe_out_size": (ctypes.c_size_t, [ctypes.c_int]),
+        "rox_set_launch_config": (ctypes.c_int, [P]),
+        "rox_get_launch_config": (ctypes.c_int, [P]),
         "rox_fp32_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P, P]),
         "rox_xsec_broadened_batch": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P,
                                                     ctypes.c_size_t, P]),
@@ -458,6 +465,22 @@ def rox_fp32_probe(n_blocks, reps, out, stream=None):
 
 def rox_fp32_probe_out_size(n_blocks):
     return int(lib.rox_fp32_probe_out_size(int(n_blocks)))
+
+
+def rox_set_launch_config(warps_per_cta=8, ctas_per_sm=0, split_rounds=1):
+    """Launch configuration of the Voigt kernel (include/rox.h); changes no result."""
+    c = RoxLaunchConfig(int(warps_per_cta), int(ctas_per_sm), int(split_rounds), 0)
+    _check(lib.rox_set_launch_config(ctypes.byref(c)))
+
+
+def rox_reset_launch_config():
+    _check(lib.rox_set_launch_config(None))
+
+
+def rox_get_launch_config():
+    c = RoxLaunchConfig()
+    _check(lib.rox_get_launch_config(ctypes.byref(c)))
+    return {"warps_per_cta": c.warps_per_cta, "ctas_per_sm": c.ctas_per_sm, "split_rounds": c.split_rounds}
 
 
 def rox_ws_status(ws, stream=None):

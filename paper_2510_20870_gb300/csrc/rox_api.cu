@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 #include "rox_internal.cuh"
@@ -32,7 +33,7 @@ cudaError_t rox_launch_tile_ranges_geo(const float4* geo, long long n_lines, lon
 size_t rox_sort_ws_bytes(long long n);
 cudaError_t rox_launch_sort(const rox_lines* in, const rox_lines_buf* out, int64_t* perm_out, void* ws,
                             cudaStream_t s);
-cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, int extras, cudaStream_t s);
+cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, int extras, int warps, cudaStream_t s);
 cudaError_t rox_launch_node_windows(const double* nu0, long long n_lines, const double* nodes, long long n,
                                     double cutoff, int32_t* jlo, int32_t* jhi, float4* geo,
                                     unsigned long long* evals, int32_t* unsorted, int32_t unsorted_value,
@@ -41,7 +42,7 @@ cudaError_t rox_launch_node_offsets(const double* nodes, long long n, long long 
                                     int32_t* status, int32_t bad_value, cudaStream_t s);
 void rox_fill_strength_consts(int convention, double T, double Q_T, double Q_ref, RoxStrengthJob* jb);
 cudaError_t rox_launch_strengths_jobs(const RoxStrengthJobs& J, long long max_count, cudaStream_t s);
-cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes, bool pre);
+cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes, bool pre, int warps);
 cudaError_t rox_launch_line_params(const RoxListDev& L, const RoxJobDev& J, float4* rec, cudaStream_t s);
 cudaError_t rox_launch_select(const double* nu0, const double* S_T, long long n, int n_temps,
                               const unsigned long long* smax_bits, double origin, double width, long long n_bins,
@@ -295,26 +296,41 @@ int select_bins(const rox_select* sel, const rox_grid* g, double cutoff, double*
   return ROX_OK;
 }
 
-int g_voigt_blocks[3] = {0, 0, 0};
-int g_voigt_device[3] = {-1, -1, -1};
+// Launch configuration of the Voigt kernel (rox_set_launch_config): warps per CTA, CTAs per SM
+// (0: as many as fit), rounds of warps' worth of items split into parts at the end of a launch.
+// None of them changes a result.
+std::mutex g_cfg_mu;
+rox_launch_config g_cfg = {8, 0, 1, 0};
+rox_launch_config launch_config() {
+  std::lock_guard<std::mutex> lock(g_cfg_mu);
+  return g_cfg;
+}
 
-// persistent grid of the Voigt kernel on the current device (uniform grid, nodes, or the
-// instantiation with precomputed per-line constants)
-int voigt_grid(int* out, bool nodes = false, bool pre = false) {
+// resident CTAs per SM of each instantiation (uniform grid, nodes, precomputed per-line
+// constants) and warps per CTA (4, 8) on the current device
+int g_voigt_per_sm[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+int g_voigt_sms[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+int g_voigt_device[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
+
+// persistent grid of the Voigt kernel on the current device for the launch configuration cfg
+int voigt_grid(int* out, const rox_launch_config& cfg, bool nodes = false, bool pre = false) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
-  const int v = pre ? 2 : (nodes ? 1 : 0);
-  if (dev != g_voigt_device[v]) {
+  const int v = pre ? 2 : (nodes ? 1 : 0), wi = cfg.warps_per_cta == 4 ? 0 : 1;
+  if (dev != g_voigt_device[v][wi]) {
     int sms = 0, per = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_check(e, "cudaDeviceGetAttribute");
-    e = rox_voigt_blocks_per_sm(&per, nodes, pre);
+    e = rox_voigt_blocks_per_sm(&per, nodes, pre, cfg.warps_per_cta);
     if (e != cudaSuccess) return cuda_check(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    g_voigt_blocks[v] = sms * (per > 0 ? per : 1);
-    g_voigt_device[v] = dev;
+    g_voigt_per_sm[v][wi] = per > 0 ? per : 1;
+    g_voigt_sms[v][wi] = sms;
+    g_voigt_device[v][wi] = dev;
   }
-  *out = g_voigt_blocks[v];
+  int per = g_voigt_per_sm[v][wi];
+  if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per) per = cfg.ctas_per_sm;
+  *out = g_voigt_sms[v][wi] * per;
   return ROX_OK;
 }
 
@@ -323,7 +339,7 @@ int voigt_grid(int* out, bool nodes = false, bool pre = false) {
 // up to tail_cap and half a round of the launch's warps, are split into their parts.
 int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* jobs, int n_jobs, RoxWsHeader* hdr,
                       float* tail_part, int32_t* tail_cnt, long long tail_cap, int nblocks, cudaStream_t s,
-                      bool nodes = false, int extras = 0) {
+                      const rox_launch_config& cfg, bool nodes = false, int extras = 0) {
   static thread_local RoxVoigtArgs A;   // ~30 KB of per-job parameters, passed by value
   A.hdr = hdr;
   A.tail_part = tail_part;
@@ -340,8 +356,8 @@ int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* job
     const int blocks = items < nblocks ? items : nblocks;
     // whole items in complete rounds of the launch's warps, then at least one round of items in
     // parts, so the launch ends in pieces of 1/ROX_PARTS of an item
-    const long long warps = (long long)blocks * ROX_WARPS;
-    long long split = items <= warps ? items : items % warps + warps;
+    const long long warps = (long long)blocks * cfg.warps_per_cta;
+    long long split = items <= warps ? items : items % warps + (long long)cfg.split_rounds * warps;
     if (split > items) split = items;
     if (split > tail_cap) split = tail_cap;
     A.n_jobs = nj;
@@ -353,7 +369,7 @@ int launch_voigt_jobs(const RoxListDev* lists, int n_lists, const RoxJobDev* job
     if (split > 0 && (rc = cuda_check(cudaMemsetAsync(tail_cnt, 0, (size_t)split * 4, s), "memset"))) return rc;
     if (j0 == 0 && g_prof_start && (rc = cuda_check(cudaEventRecord(g_prof_start, s), "cudaEventRecord"))) return rc;
     if (items == 0) continue;
-    if ((rc = cuda_check(rox_launch_voigt(A, blocks, nodes, extras, s), "voigt kernel"))) return rc;
+    if ((rc = cuda_check(rox_launch_voigt(A, blocks, nodes, extras, cfg.warps_per_cta, s), "voigt kernel"))) return rc;
   }
   if (g_prof_stop) return cuda_check(cudaEventRecord(g_prof_stop, s), "cudaEventRecord");
   return ROX_OK;
@@ -507,8 +523,9 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   if (ws_bytes < w.bytes) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, w.bytes);
 
   cudaStream_t s = (cudaStream_t)stream;
+  const rox_launch_config cfg = launch_config();
   int nblocks = 0;
-  if ((rc = voigt_grid(&nblocks, on_nodes, pre))) return rc;
+  if ((rc = voigt_grid(&nblocks, cfg, on_nodes, pre))) return rc;
   const long long nt = n_tiles_of(n_grid);
   const long long nl = lines->n;
 
@@ -611,7 +628,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
           jg.back().list = tidx[k] - g0;
         }
       if ((rc = launch_voigt_jobs(Ls, ng, jg.data(), (int)jg.size(), w.hdr, w.tail_part, w.tail_cnt, w.tail_cap,
-                                  nblocks, s, false, ROX_VX_INDEX)))
+                                  nblocks, s, cfg, false, ROX_VX_INDEX)))
         return rc;
     }
     return ok();
@@ -619,7 +636,7 @@ int xsec_batch_impl(const rox_lines* lines, const rox_grid* grid, const rox_node
   if (pre && (rc = cuda_check(rox_launch_line_params(L0, jobs[0], w.rec, s), "line parameter kernel"))) return rc;
   const int extras = br ? ROX_VX_BROAD : (pre ? ROX_VX_PRE : 0);
   if ((rc = launch_voigt_jobs(&L0, 1, jobs.data(), n_pt, w.hdr, w.tail_part, w.tail_cnt, w.tail_cap, nblocks, s,
-                              on_nodes, extras)))
+                              cfg, on_nodes, extras)))
     return rc;
   return ok();
 }
@@ -904,7 +921,8 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
   const size_t need = jobs_layout(jobs, n_jobs, nullptr, nullptr, nullptr, nullptr);
   if (ws_bytes < need) return fail(ROX_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, need);
   int nblocks = 0;
-  if ((rc = voigt_grid(&nblocks))) return rc;
+  const rox_launch_config cfg = launch_config();
+  if ((rc = voigt_grid(&nblocks, cfg))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   RoxWsHeader* hdr = (RoxWsHeader*)ws;
   std::vector<double*> S64(n_jobs);
@@ -986,8 +1004,28 @@ int rox_xsec_jobs(const rox_prepared* lists, int n_lists, const rox_job* jobs, i
     d.flags = j.flags;
     d.t_row = 0;
   }
-  if ((rc = launch_voigt_jobs(L, n_lists, J.data(), n_jobs, hdr, tail.part, tail.cnt, tail.cap, nblocks, s)))
+  if ((rc = launch_voigt_jobs(L, n_lists, J.data(), n_jobs, hdr, tail.part, tail.cnt, tail.cap, nblocks, s, cfg)))
     return rc;
+  return ok();
+}
+
+int rox_set_launch_config(const rox_launch_config* cfg) {
+  rox_launch_config c = {8, 0, 1, 0};
+  if (cfg) {
+    if (cfg->warps_per_cta != 4 && cfg->warps_per_cta != 8) return fail(ROX_EINVAL, "warps_per_cta must be 4 or 8");
+    if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 64) return fail(ROX_EINVAL, "ctas_per_sm must be 0..64");
+    if (cfg->split_rounds < 1 || cfg->split_rounds > 4) return fail(ROX_EINVAL, "split_rounds must be 1..4");
+    c = *cfg;
+    c.pad = 0;
+  }
+  std::lock_guard<std::mutex> lock(g_cfg_mu);
+  g_cfg = c;
+  return ok();
+}
+
+int rox_get_launch_config(rox_launch_config* out) {
+  if (!out) return fail(ROX_EINVAL, "out is NULL");
+  *out = launch_config();
   return ok();
 }
 

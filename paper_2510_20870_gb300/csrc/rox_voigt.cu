@@ -404,24 +404,24 @@ __global__ void k_line_params(const RoxListDev L, const RoxJobDev J, float4* rec
 // then count positions in that index) and ROX_VX_BROAD (widths from the broadening pass). Each
 // extra is compiled only into the instantiations that use it: in this kernel even a few added
 // instructions per line batch cost several percent of the plain launch.
-template <bool NU, int X>
-__global__ void __launch_bounds__(ROX_THREADS, 3) k_voigt(const __grid_constant__ RoxVoigtArgs A) {
+template <bool NU, int X, int W>
+__global__ void __launch_bounds__(W * 32, 24 / W) k_voigt(const __grid_constant__ RoxVoigtArgs A) {
   constexpr bool IDX = (X & ROX_VX_INDEX) != 0;
   constexpr bool BRD = (X & ROX_VX_BROAD) != 0;
   constexpr bool PRE = (X & ROX_VX_PRE) != 0;
   extern __shared__ __align__(16) float2 s_nodes[];   // NU: node offsets; PRE: the staged per-line constants
-  __shared__ float4 s_geo[ROX_WARPS][2][32];
-  __shared__ float s_S[ROX_WARPS][2][32];
-  __shared__ PairTab s_pairs[ROX_WARPS];
-  __shared__ LineTab s_lines[ROX_WARPS];
-  __shared__ float s_zacc[ROX_WARPS][ROX_SPAN];
-  __shared__ float s_tot[ROX_WARPS][ROX_SPAN];    // the span's sum over its parts
+  __shared__ float4 s_geo[W][2][32];
+  __shared__ float s_S[W][2][32];
+  __shared__ PairTab s_pairs[W];
+  __shared__ LineTab s_lines[W];
+  __shared__ float s_zacc[W][ROX_SPAN];
+  __shared__ float s_tot[W][ROX_SPAN];    // the span's sum over its parts
   __shared__ float s_daw[ROX_NDAW];
   __shared__ int s_status;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, w = tid >> 5;
-  for (int i = tid; i < ROX_NDAW; i += ROX_THREADS) s_daw[i] = (&rox_daw_taylor[0][0])[i];
+  for (int i = tid; i < ROX_NDAW; i += W * 32) s_daw[i] = (&rox_daw_taylor[0][0])[i];
   if (tid == 0) s_status = *(volatile int32_t*)&A.hdr->status;
   __syncthreads();
   if (s_status != ROX_OK) return;   // e.g. unsorted input: leave sigma untouched
@@ -740,8 +740,15 @@ __global__ void k_faddeeva(const float* x, const float* y, float* out, long long
 
 }  // namespace
 
-#define ROX_NODES_SMEM (ROX_WARPS * ROX_SPAN * sizeof(float2))
-#define ROX_PRE_SMEM (ROX_WARPS * 2 * 32 * 3 * sizeof(float4))
+namespace {
+// dynamic shared memory of an instantiation with W warps per CTA: the node rows (NU) or the
+// staged per-line constants (ROX_VX_PRE)
+template <bool NU, int X, int W>
+constexpr size_t voigt_dyn_smem() {
+  return NU ? (size_t)W * ROX_SPAN * sizeof(float2)
+            : ((X & ROX_VX_PRE) ? (size_t)W * 2 * 32 * 3 * sizeof(float4) : (size_t)0);
+}
+}  // namespace
 
 // per-line constants of job J (one (P,T) point) for its lines [J.l0, J.l1): rec[3 i .. 3 i + 2]
 cudaError_t rox_launch_line_params(const RoxListDev& L, const RoxJobDev& J, float4* rec, cudaStream_t s) {
@@ -753,45 +760,64 @@ cudaError_t rox_launch_line_params(const RoxListDev& L, const RoxJobDev& J, floa
   return cudaGetLastError();
 }
 
-cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, int extras, cudaStream_t s) {
-  if (nodes) {
-    if (extras) return cudaErrorNotSupported;   // no caller combines nodes with a selection or broadening
-    // static shared memory plus the node rows exceed 48 KB: opt in (idempotent, per device)
-    cudaError_t e = cudaFuncSetAttribute(k_voigt<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ROX_NODES_SMEM);
+namespace {
+
+template <bool NU, int X, int W>
+cudaError_t launch_k(const RoxVoigtArgs& A, int n_blocks, cudaStream_t s) {
+  constexpr size_t dyn = voigt_dyn_smem<NU, X, W>();
+  if (dyn) {   // static shared memory plus these exceed 48 KB: opt in (idempotent, per device)
+    cudaError_t e = cudaFuncSetAttribute(k_voigt<NU, X, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    k_voigt<true, 0><<<n_blocks, ROX_THREADS, ROX_NODES_SMEM, s>>>(A);
-  } else if (extras == 0) {
-    k_voigt<false, 0><<<n_blocks, ROX_THREADS, 0, s>>>(A);
-  } else if (extras == ROX_VX_INDEX) {
-    k_voigt<false, ROX_VX_INDEX><<<n_blocks, ROX_THREADS, 0, s>>>(A);
-  } else if (extras == ROX_VX_BROAD) {
-    k_voigt<false, ROX_VX_BROAD><<<n_blocks, ROX_THREADS, 0, s>>>(A);
-  } else if (extras == ROX_VX_PRE) {
-    cudaError_t e = cudaFuncSetAttribute(k_voigt<false, ROX_VX_PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ROX_PRE_SMEM);
-    if (e != cudaSuccess) return e;
-    k_voigt<false, ROX_VX_PRE><<<n_blocks, ROX_THREADS, ROX_PRE_SMEM, s>>>(A);
-  } else {
-    return cudaErrorNotSupported;   // no entry point combines an indexed list with broadening
   }
+  k_voigt<NU, X, W><<<n_blocks, W * 32, dyn, s>>>(A);
   return cudaGetLastError();
 }
 
-cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes, bool pre) {
-  if (pre) {
-    cudaError_t e = cudaFuncSetAttribute(k_voigt<false, ROX_VX_PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ROX_PRE_SMEM);
+template <bool NU, int X, int W>
+cudaError_t blocks_k(int* nb) {
+  constexpr size_t dyn = voigt_dyn_smem<NU, X, W>();
+  if (dyn) {
+    cudaError_t e = cudaFuncSetAttribute(k_voigt<NU, X, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<false, ROX_VX_PRE>, ROX_THREADS, ROX_PRE_SMEM);
   }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<NU, X, W>, W * 32, dyn);
+}
+
+template <int W>
+cudaError_t launch_w(const RoxVoigtArgs& A, int n_blocks, bool nodes, int extras, cudaStream_t s) {
   if (nodes) {
-    cudaError_t e = cudaFuncSetAttribute(k_voigt<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ROX_NODES_SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<true, 0>, ROX_THREADS, ROX_NODES_SMEM);
+    if (extras) return cudaErrorNotSupported;   // no caller combines nodes with a selection or broadening
+    return launch_k<true, 0, W>(A, n_blocks, s);
   }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_voigt<false, 0>, ROX_THREADS, 0);
+  switch (extras) {
+    case 0: return launch_k<false, 0, W>(A, n_blocks, s);
+    case ROX_VX_INDEX: return launch_k<false, ROX_VX_INDEX, W>(A, n_blocks, s);
+    case ROX_VX_BROAD: return launch_k<false, ROX_VX_BROAD, W>(A, n_blocks, s);
+    case ROX_VX_PRE: return launch_k<false, ROX_VX_PRE, W>(A, n_blocks, s);
+    default: return cudaErrorNotSupported;   // no entry point combines these extras
+  }
+}
+
+template <int W>
+cudaError_t blocks_w(int* nb, bool nodes, bool pre) {
+  if (pre) return blocks_k<false, ROX_VX_PRE, W>(nb);
+  if (nodes) return blocks_k<true, 0, W>(nb);
+  return blocks_k<false, 0, W>(nb);
+}
+
+}  // namespace
+
+// warps: warps per CTA of the launch (4 or 8; the launch configuration of rox_launch_config)
+cudaError_t rox_launch_voigt(const RoxVoigtArgs& A, int n_blocks, bool nodes, int extras, int warps, cudaStream_t s) {
+  if (warps == 4) return launch_w<4>(A, n_blocks, nodes, extras, s);
+  if (warps == 8) return launch_w<8>(A, n_blocks, nodes, extras, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes, bool pre, int warps) {
+  if (warps == 4) return blocks_w<4>(nb, nodes, pre);
+  if (warps == 8) return blocks_w<8>(nb, nodes, pre);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t rox_launch_faddeeva(const float* x, const float* y, float* out, long long n, cudaStream_t s) {

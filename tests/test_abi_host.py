@@ -213,3 +213,17 @@ def test_extension_arguments_rejected_on_host(lib):
     assert L.rox_xsec_nodes_batch(by(hit), by(N), *args, 0.0, 0, 8, 256, 1 << 30, None) == E
     assert L.rox_xsec_nodes_batch(by(hit), by(N), *args, 5000.0, 0, 8, 256, 1 << 30, None) == lib.ROX_ERANGE
     assert L.rox_xsec_nodes_batch(by(hit), by(N), *args, 25.0, 0, 8, 256, 16, None) == lib.ROX_ENOMEM
+
+
+def test_launch_config_validation(lib):
+    """rox_set_launch_config refuses out-of-range knobs and changes nothing then; NULL restores
+    the defaults (host-only calls)."""
+    import paper_2510_20870_gb300 as rox
+    rox.rox_set_launch_config(4, 2, 3)
+    assert rox.rox_get_launch_config() == {"warps_per_cta": 4, "ctas_per_sm": 2, "split_rounds": 3}
+    for bad in [(6, 0, 1), (8, -1, 1), (8, 0, 0), (8, 0, 5)]:
+        with pytest.raises(rox.RoxError):
+            rox.rox_set_launch_config(*bad)
+        assert rox.rox_get_launch_config()["warps_per_cta"] == 4
+    rox.rox_reset_launch_config()
+    assert rox.rox_get_launch_config() == {"warps_per_cta": 8, "ctas_per_sm": 0, "split_rounds": 1}

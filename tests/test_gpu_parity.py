@@ -373,3 +373,26 @@ def test_shards_on_one_gpu_reassemble_the_unsharded_result():
             rox.rox_xsec_jobs([prep], [job], ws)
             pieces.append(o.double().cpu().numpy())
         check_sigma(np.concatenate(pieces), full[k], rel_tol=1e-6, label="wavenumber shards")
+
+
+def test_launch_configurations_change_no_result():
+    """The autotuner's knobs (warps per CTA, CTAs per SM, split rounds) select other
+    instantiations and grids of the Voigt kernel; every one gives the same cross-section bit for
+    bit, and it matches the oracle."""
+    w, L = _small_lines(1, 30000, 290.0, 1330.0, 41)
+    grid = (300.0, 0.01, 100001)
+    pts = [(0.1, 1500.0, q_pair(w, 1500.0)[0])]
+    Qr = q_pair(w, 296.0)[1]
+    dl = to_device(L, torch)
+    outs = []
+    try:
+        for cfg in [(8, 0, 1), (4, 0, 1), (4, 3, 2), (8, 1, 2)]:
+            rox.rox_set_launch_config(*cfg)
+            assert rox.rox_get_launch_config()["warps_per_cta"] == cfg[0]
+            outs.append(_run_xsec(dl, grid, pts, Qr, w.mass_amu, 25.0, flags=rox.ROX_KAHAN)[0])
+    finally:
+        rox.rox_reset_launch_config()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    ref = oracle.xsec_window(L, grid, 40000, 40200, 0.1, 1500.0, pts[0][2], Qr, w.mass_amu, 25.0)
+    check_sigma(outs[0][0, 40000:40200], ref, M=float(outs[0][0].max()), label="launch configurations")
