@@ -462,7 +462,9 @@ __global__ void __launch_bounds__(W * 32, 24 / W) k_voigt(const __grid_constant_
     const int local = item - (k > 0 ? A.item_end[k - 1] : 0);
     const int span = J.span_first + J.n_spans - 1 - local;       // wide-line (high nu) spans first
     const int f16 = Lst.width_f16;
-    const bool kahan = (J.flags & ROX_KAHAN) != 0;
+    // compensation weight of the part sums: 1 (ROX_KAHAN) keeps the Kahan correction term, 0
+    // zeroes it, which leaves the plain sum (one branch-free form for both)
+    const float kw = (J.flags & ROX_KAHAN) ? 1.0f : 0.0f;
     const float dnu_f = Lst.dnu_f;
     // offsets on a uniform grid round once more (X0 + 32 m dnu), hence the precision margin
     const float margin_cm = NU ? 0.0f : fast_margin(dnu_f);
@@ -647,39 +649,26 @@ __global__ void __launch_bounds__(W * 32, 24 / W) k_voigt(const __grid_constant_
           zone_line<NU>(PT, LT, __ffs(z) - 1, Aw, lane, lanef, dnu_f, Lst.inv_dnu_f, s_daw, D, zacc);
         __syncwarp();
         // the partial sums into the part's total every 4 batches: compensated (Kahan) with
-        // ROX_KAHAN, else plainly
+        // ROX_KAHAN, else plainly (kw = 0: the correction term stays 0)
         if ((nb & 3) == 3 || b0 + 32 >= phi) {
-          if (kahan) {
 #pragma unroll
-            for (int m = 0; m < ROX_K; m++) {
-              const float yk = acc[m] - cmp[m];
-              const float tk = tot[m] + yk;
-              cmp[m] = (tk - tot[m]) - yk;
-              tot[m] = tk;
-              acc[m] = 0.f;
-            }
-          } else {
-#pragma unroll
-            for (int m = 0; m < ROX_K; m++) {
-              tot[m] += acc[m];
-              acc[m] = 0.f;
-            }
+          for (int m = 0; m < ROX_K; m++) {
+            const float yk = acc[m] - cmp[m];
+            const float tk = tot[m] + yk;
+            cmp[m] = ((tk - tot[m]) - yk) * kw;
+            tot[m] = tk;
+            acc[m] = 0.f;
           }
         }
       }
       cp_async_wait0();
       // fold in the pass-2 (near-centre) sums
-      if (kahan) {
 #pragma unroll
-        for (int m = 0; m < ROX_K; m++) {
-          const float yk = zacc[32 * m + lane] - cmp[m];
-          const float tk = tot[m] + yk;
-          cmp[m] = (tk - tot[m]) - yk;
-          tot[m] = tk;
-        }
-      } else {
-#pragma unroll
-        for (int m = 0; m < ROX_K; m++) tot[m] += zacc[32 * m + lane];
+      for (int m = 0; m < ROX_K; m++) {
+        const float yk = zacc[32 * m + lane] - cmp[m];
+        const float tk = tot[m] + yk;
+        cmp[m] = ((tk - tot[m]) - yk) * kw;
+        tot[m] = tk;
       }
       if (part >= 0) {           // a split item: this part's sum goes to the tail scratch
         float* dst = A.tail_part + ((size_t)(item - A.n_whole) * ROX_PARTS + p) * ROX_SPAN;

@@ -396,3 +396,25 @@ def test_launch_configurations_change_no_result():
         assert np.array_equal(o, outs[0])
     ref = oracle.xsec_window(L, grid, 40000, 40200, 0.1, 1500.0, pts[0][2], Qr, w.mass_amu, 25.0)
     check_sigma(outs[0][0, 40000:40200], ref, M=float(outs[0][0].max()), label="launch configurations")
+
+
+def test_compensated_and_plain_summation_both_in_use():
+    """A list of equal strengths and wide (10 bar) lines: every point sums thousands of terms of
+    similar size, so ROX_KAHAN and the plain sum round differently somewhere; both match the
+    oracle."""
+    w, L = _small_lines(0, 60000, 1000.0, 1060.0, 7)
+    L = dict(L)
+    L["s_or_a"] = np.full(len(L["nu0"]), 1e-20, dtype=np.float32)
+    L["e_lower"] = np.zeros(len(L["nu0"]), dtype=np.float32)
+    grid = (1000.0, 0.01, 6001)
+    Qt, Qr = q_pair(w, 1000.0)
+    dl = to_device(L, torch)
+    plain = _run_xsec(dl, grid, [(10.0, 1000.0, Qt)], Qr, w.mass_amu, 25.0, flags=0)[0][0]
+    comp = _run_xsec(dl, grid, [(10.0, 1000.0, Qt)], Qr, w.mass_amu, 25.0, flags=rox.ROX_KAHAN)[0][0]
+    assert np.any(plain != comp)
+    for a in (0, 2900, 5937):
+        ref = oracle.xsec_window(L, grid, a, a + 64, 10.0, 1000.0, Qt, Qr, w.mass_amu, 25.0)
+        M = float(comp.max())
+        e_p = check_sigma(plain[a:a + 64], ref, M=M, label="plain sum %d" % a)
+        e_c = check_sigma(comp[a:a + 64], ref, M=M, label="compensated sum %d" % a)
+        print("PARITY summation window %d: plain %.3e compensated %.3e" % (a, e_p, e_c))
