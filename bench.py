@@ -41,9 +41,9 @@ VOIGT_TRAFFIC_BYTES = 3.037e8
 # DRAM bytes of one k_cia_grid launch on the CIA workload (ncu dram__bytes_read + write,
 # profiles/k_cia_grid_40T_2970001pts.md; part of the 950 MB output is still in L2 at the end)
 CIA_TRAFFIC_BYTES = 9.086e8
-# DRAM bytes per evaluation of k_voigt on the large list (ncu dram__bytes_read + write on one
-# 1e7-line chunk of it, divided by that launch's evaluations); None until captured
-VOIGT_TRAFFIC_LARGE = None
+# DRAM bytes per evaluation of k_voigt on the large list: ncu dram__bytes_read + write on one
+# 1e7-line chunk of it (4.402 GB for 1.989e11 evaluations, profiles/k_voigt_large_1e7_chunk.md)
+VOIGT_TRAFFIC_LARGE = 4.402e9 / 1.989e11
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "Voigt line-profile evals/s"
