@@ -134,6 +134,20 @@ def test_stream_1e9_subsample_chunked(pool):
     L = oracle.sort_lines(rs.make_lines(w, 0, n_sub))
     rng = np.random.default_rng(4)
     starts = [0, grid[2] - 64] + [int(s) for s in rng.integers(0, grid[2] - 64, 14)]
+    # the strengths span 17 decades, so most random windows lie below 1e-6 M (checked against the
+    # absolute floor only); add 8 windows around the largest peaks, where the relative bound bites
+    order = np.argsort(chunked)[::-1]
+    peaks = []
+    for j in order:
+        if all(abs(int(j) - p) > 5000 for p in peaks):
+            peaks.append(int(j))
+        if len(peaks) == 8:
+            break
+    starts += [min(max(p - 32, 0), grid[2] - 64) for p in peaks]
     tasks = [(L, grid, s, s + 64, P, T, Qt, Qr, w.mass_amu, w.cutoff) for s in starts]
+    checked, worst = 0, 0.0
     for s, ref in zip(starts, pool.map(_oracle_window, tasks, chunksize=1)):
-        check_sigma(chunked[s:s + 64], ref, M=M, label="window %d" % s)
+        worst = max(worst, check_sigma(chunked[s:s + 64], ref, M=M, label="large subsample window %d" % s))
+        checked += int(np.sum(ref > 1e-6 * M))
+    assert checked >= 8 * 64 // 2          # the peak windows are checked against the relative bound
+    print("PARITY large subsample, %d windows: worst %.3e over %d points" % (len(starts), worst, checked))
