@@ -155,6 +155,15 @@ ROX_FN rox_c rox_cmul(rox_c a, rox_c b) {
   return o;
 }
 
+// One complex Horner step with a real coefficient, acc * m + c, in four FP32 operations (the
+// coefficient enters the real part's FMA chain instead of a separate add).
+ROX_FN rox_c rox_horner_step(rox_c acc, rox_c m, float c) {
+  rox_c o;
+  o.r = fmaf(acc.r, m.r, fmaf(-acc.i, m.i, c));
+  o.i = fmaf(acc.r, m.i, acc.i * m.r);
+  return o;
+}
+
 // Horner in zeta = z^2 with real coefficients c[0..n-1] (highest first)
 template <int N>
 ROX_FN rox_c rox_horner_zeta(const float* c, rox_c zeta) {
@@ -162,11 +171,7 @@ ROX_FN rox_c rox_horner_zeta(const float* c, rox_c zeta) {
   acc.r = c[0];
   acc.i = 0.0f;
 #pragma unroll
-  for (int k = 1; k < N; k++) {
-    rox_c m = rox_cmul(acc, zeta);
-    acc.r = m.r + c[k];
-    acc.i = m.i;
-  }
+  for (int k = 1; k < N; k++) acc = rox_horner_step(acc, zeta, c[k]);
   return acc;
 }
 
@@ -219,11 +224,7 @@ ROX_FN float rox_re_w_weideman(float x, float y) {
   p.r = rox_wei_a[0];
   p.i = 0.0f;
 #pragma unroll
-  for (int k = 1; k < ROX_WEI_N; k++) {
-    rox_c m = rox_cmul(p, Z);
-    p.r = m.r + rox_wei_a[k];
-    p.i = m.i;
-  }
+  for (int k = 1; k < ROX_WEI_N; k++) p = rox_horner_step(p, Z, rox_wei_a[k]);
   rox_c t = rox_cmul(p, q);                          // p/(L - iz)
   t.r = fmaf(2.0f, t.r, ROX_INV_SQRT_PI);
   t.i = 2.0f * t.i;
