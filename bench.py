@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true",
                     help="sweep the Voigt launch configuration (paper_2510_20870_gb300/autotune.py) on the large "
                          "list's 1e8-line chunk and on the exomol list, write the cache and print the results")
+    ap.add_argument("--probes", action="store_true",
+                    help="print the FP32 probes only: the FMA peak and the Voigt pair loop's standalone rate")
     return ap.parse_args()
 
 
@@ -658,6 +660,32 @@ def fp32_peaks(dev_index, sms):
                              "(CUDA events)" % (nb, fma, ms)}
     if c.get("sm_mhz"):
         res["measured_fma_per_sm_clock"] = fma / (ms * 1e-3) / (sms * c["sm_mhz"] * 1e6)
+    res.update(loop_ceilings(dev_index, sms, out))
+    return res
+
+
+def loop_ceilings(dev_index, sms, out):
+    """The attainable rate of the Voigt kernel's inner loop: its pass-1 pair loop run alone
+    (rox_pair_loop_probe), timed with CUDA events while nvidia-smi samples the SM clock."""
+    import torch
+    from paper_2510_20870_gb300 import _binding as rb
+    nb = sms * 3
+    rb.rox_pair_loop_probe(nb, 10, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev_index) as clk:
+        time.sleep(0.1)
+        e0.record()
+        ev = sum(rb.rox_pair_loop_probe(nb, 1_000, out) for _ in range(20))
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    mhz = clk.summary().get("sm_mhz")
+    res = {"pair_loop_evals_s": ev / (ms * 1e-3),
+           "pair_loop_basis": "rox_pair_loop_probe: %d blocks x 256 threads, %.3g evaluations in %.1f ms (CUDA "
+                              "events), SM clock %s MHz" % (nb, ev, ms, mhz)}
+    if mhz:
+        res["pair_loop_evals_per_sm_clock"] = ev / (ms * 1e-3) / (sms * mhz * 1e6)
     return res
 
 
@@ -669,6 +697,10 @@ def voigt_roofline(evals, kernel_ms, peaks, traffic, traffic_note, clocks):
             "peak_basis": peaks["formula_basis"], "flops_per_eval": FLOPS_PER_EVAL,
             "peak_measured": peaks["measured_tflops"], "frac_of_measured": achieved / peaks["measured_tflops"],
             "peak_measured_basis": peaks["measured_basis"], "peak_measured_sm_mhz": peaks.get("measured_sm_mhz")}
+    if peaks.get("pair_loop_evals_s"):
+        roof["pair_loop_ceiling_evals_s"] = peaks["pair_loop_evals_s"]
+        roof["frac_of_pair_loop"] = evals / (kernel_ms * 1e-3) / peaks["pair_loop_evals_s"]
+        roof["pair_loop_basis"] = peaks["pair_loop_basis"]
     if clocks.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / (peak * clocks["sm_mhz"] / SM_MAX_MHZ)
     return roof
@@ -1195,6 +1227,12 @@ def main():
     args = parse()
     if args.autotune:
         run_autotune(args)
+        return
+    if args.probes:
+        import torch
+        torch.cuda.set_device(0)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        print(json.dumps({"probes": fp32_peaks(0, sms), "device": torch.cuda.get_device_name(0)}))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -430,6 +430,16 @@ int rox_get_launch_config(rox_launch_config* out);
 size_t rox_fp32_probe_out_size(int n_blocks);
 int rox_fp32_probe(int n_blocks, int reps, float* out, size_t out_bytes, double* fma_out, void* stream);
 
+/* Measurement helper: the attainable rate of the Voigt kernel's inner loop. Runs the pass-1
+ * pair loop of the cross-section kernel (two lines per reciprocal, far form, no clamp or mask)
+ * alone on synthetic far-wing constants, n_blocks blocks of 256 threads (8 warps, as the
+ * kernel's default launch), each warp walking 16 pairs reps times over its span of ROX_SPAN
+ * points; no line set-up, staging, window edges or slow zones. out as rox_fp32_probe
+ * (rox_fp32_probe_out_size(n_blocks) bytes, device). *evals_out (host) receives the
+ * (line, point) evaluations the launch performs; time it with events on `stream`. Errors as
+ * rox_fp32_probe. */
+int rox_pair_loop_probe(int n_blocks, int reps, float* out, size_t out_bytes, double* evals_out, void* stream);
+
 /* Allocation-free variant of rox_xsec (one (P,T) point), for callers that cannot
  * allocate device memory themselves: an application whose own memory manager owns all
  * device memory, a plugin that is not allowed to call cudaMalloc, or an interface that

@@ -127,6 +127,7 @@ def _load():
         "rox_set_launch_config": (ctypes.c_int, [P]),
         "rox_get_launch_config": (ctypes.c_int, [P]),
         "rox_fp32_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P, P]),
+        "rox_pair_loop_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P, P]),
         "rox_xsec_broadened_batch": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P, P, D, D, D, U, P, P,
                                                     ctypes.c_size_t, P]),
     }
@@ -465,6 +466,14 @@ def rox_fp32_probe(n_blocks, reps, out, stream=None):
 
 def rox_fp32_probe_out_size(n_blocks):
     return int(lib.rox_fp32_probe_out_size(int(n_blocks)))
+
+
+def rox_pair_loop_probe(n_blocks, reps, out, stream=None):
+    """Launch the Voigt pair-loop probe (include/rox.h); returns the (line, point) evaluations it performs."""
+    ev = ctypes.c_double(0.0)
+    _check(lib.rox_pair_loop_probe(int(n_blocks), int(reps), _ptr(out), out.numel() * out.element_size(),
+                                   ctypes.byref(ev), _stream(stream)))
+    return ev.value
 
 
 def rox_set_launch_config(warps_per_cta=8, ctas_per_sm=0, split_rounds=1):

@@ -5,6 +5,7 @@
 #include "rox_internal.cuh"
 
 int rox_set_error(int code, const char* msg);   // rox_api.cu
+cudaError_t rox_launch_pair_loop_probe(int n_blocks, int warps, int reps, float* out, cudaStream_t s);   // rox_voigt.cu
 
 namespace {
 
@@ -42,5 +43,16 @@ extern "C" int rox_fp32_probe(int n_blocks, int reps, float* out, size_t out_byt
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rox_set_error(ROX_ECUDA, cudaGetErrorString(e));
   *fma_out = (double)n_blocks * ROX_PROBE_THREADS * (double)reps * ROX_PROBE_UNROLL * ROX_PROBE_CHAINS;
+  return ROX_OK;
+}
+
+extern "C" int rox_pair_loop_probe(int n_blocks, int reps, float* out, size_t out_bytes, double* evals_out,
+                                   void* stream) {
+  if (n_blocks < 1 || reps < 1 || !out || !evals_out) return rox_set_error(ROX_EINVAL, "rox_pair_loop_probe: bad arguments");
+  if (out_bytes < rox_fp32_probe_out_size(n_blocks)) return rox_set_error(ROX_ENOMEM, "rox_pair_loop_probe: out too small");
+  cudaError_t e = rox_launch_pair_loop_probe(n_blocks, ROX_PROBE_THREADS / 32, reps, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return rox_set_error(ROX_ECUDA, cudaGetErrorString(e));
+  // per thread: reps rounds x 16 pairs x 2 lines x ROX_K points
+  *evals_out = (double)n_blocks * ROX_PROBE_THREADS * (double)reps * 16.0 * 2.0 * ROX_K;
   return ROX_OK;
 }

@@ -721,6 +721,38 @@ __global__ void __launch_bounds__(W * 32, 24 / W) k_voigt(const __grid_constant_
   if (lane == 0 && evals) atomicAdd(&A.hdr->evals_total, evals);
 }
 
+// Probe of the attainable rate of pass 1's inner loop: cover_pair for clean pairs (the code
+// k_voigt runs for most pairs), alone, with W warps per CTA as k_voigt's launch, on synthetic
+// far-wing constants held in each warp's pair table (offsets of 3-8 cm^-1, so no clamp or mask
+// applies). Each warp walks its 16 pairs `reps` times; no line set-up, staging, edges or slow
+// zones. Not part of the cross-section method.
+template <int W>
+__global__ void __launch_bounds__(W * 32, 24 / W) k_pair_loop_probe(float* out, int reps, float dnu_f) {
+  __shared__ PairTab s_pairs[W];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  PairTab& PT = s_pairs[w];
+  if (lane < 16) {
+    const float i0 = (float)(2 * lane), i1 = (float)(2 * lane + 1);
+    PT.ab[lane] = make_float4(1.0e-4f * (1.0f + i0), 1.0e-4f * (1.0f + i1), 1.0e-8f * (1.0f + i0), 1.0e-8f * (1.0f + i1));
+    PT.pq[lane] = make_float4(1.0e-3f, 1.1e-3f, 2.0e-7f, 2.1e-7f);
+    PT.ef[lane] = make_float4(-300.0f - 17.0f * i0, -300.0f - 17.0f * i1, -0.0037f * (i0 + 1.0f), -0.0037f * (i1 + 1.0f));
+    PT.tz[lane] = make_float2(0.0f, 0.0f);
+  }
+  __syncwarp();
+  float acc[ROX_K];
+#pragma unroll
+  for (int m = 0; m < ROX_K; m++) acc[m] = 0.0f;
+  const float lanef = (float)lane;
+  for (int r = 0; r < reps; r++) {
+#pragma unroll 1
+    for (int k = 0; k < 16; k++) cover_pair<false, false>(PT, k, lanef, dnu_f, nullptr, acc);
+  }
+  float t = 0.0f;
+#pragma unroll
+  for (int m = 0; m < ROX_K; m++) t += acc[m];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 __global__ void k_faddeeva(const float* x, const float* y, float* out, long long n) {
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
@@ -807,6 +839,14 @@ cudaError_t rox_voigt_blocks_per_sm(int* nb, bool nodes, bool pre, int warps) {
   if (warps == 4) return blocks_w<4>(nb, nodes, pre);
   if (warps == 8) return blocks_w<8>(nb, nodes, pre);
   return cudaErrorInvalidValue;
+}
+
+// pair-loop probe: n_blocks CTAs of `warps` warps (4 or 8); out holds n_blocks * warps * 32 floats
+cudaError_t rox_launch_pair_loop_probe(int n_blocks, int warps, int reps, float* out, cudaStream_t s) {
+  if (warps == 4) k_pair_loop_probe<4><<<n_blocks, 4 * 32, 0, s>>>(out, reps, 0.01f);
+  else if (warps == 8) k_pair_loop_probe<8><<<n_blocks, 8 * 32, 0, s>>>(out, reps, 0.01f);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
 }
 
 cudaError_t rox_launch_faddeeva(const float* x, const float* y, float* out, long long n, cudaStream_t s) {
