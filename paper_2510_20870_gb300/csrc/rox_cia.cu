@@ -151,12 +151,13 @@ __device__ long long grid_first(const CiaGrid& g, double x, bool strict) {
   return lo;
 }
 
-// Workspace of the uniform-grid path: per sample c_i (int64), the value at c_i and the step
-// (float64), per block e; unused for blocks whose temperature is not asked for.
+// Workspace of the uniform-grid path: per sample c_i (int64), the value at c_i, the step and 32
+// steps (float64), per block e; unused for blocks whose temperature is not asked for.
 struct CiaTables {
   long long* c;
   double* v0;
   double* dv;
+  double* dv32;   // 32 dv, a lane's step (exact: a power-of-two multiple)
   long long* e;
 };
 
@@ -182,16 +183,19 @@ __global__ void k_cia_intervals(const __grid_constant__ CiaArgs A, const double*
   if (q == last) {
     T.v0[q] = k[q];
     T.dv[q] = 0.0;
+    T.dv32[q] = 0.0;
     T.e[b] = grid_first(g, xi, true);
   } else {
     const double yi = k[q], dy = k[q + 1] - yi;
     const double r = 1.0 / (nu[q + 1] - xi);
     T.v0[q] = fma(dy, (grid_nu(g, c) - xi) * r, yi);
-    T.dv[q] = dy * (g.dnu * r);
+    const double dv = dy * (g.dnu * r);
+    T.dv[q] = dv;
+    T.dv32[q] = 32.0 * dv;
   }
 }
 
-__global__ void __launch_bounds__(32 * ROX_CIA_GWARPS)
+__global__ void __launch_bounds__(32 * ROX_CIA_GWARPS, 12)   // 40 registers: 12 CTAs per SM
 k_cia_grid(const __grid_constant__ CiaArgs A, const CiaGrid g, const CiaTables T, double* out) {
   const int lane = threadIdx.x & 31;
   const long long tile_pts = 32LL * ROX_CIA_GRUN;
@@ -241,9 +245,8 @@ k_cia_grid(const __grid_constant__ CiaArgs A, const CiaGrid g, const CiaTables T
             i++;
             nxt = i + 1 < m ? c[i + 1] : e;
           }
-          const double dv = T.dv[o + i];
-          val = fma((double)(j - c[i]), dv, T.v0[o + i]);
-          step = 32.0 * dv;
+          val = fma((double)(j - c[i]), T.dv[o + i], T.v0[o + i]);
+          step = T.dv32[o + i];   // no float64 multiply per set-up: the pipe this kernel is bound by
         }
         if (!((done >> s) & 1u)) row[j] = val;
         val += step;
@@ -305,7 +308,8 @@ int cia_launch(const rox_cia* cia, const double* nodes, double nu_min, double dn
     tb.c = (long long*)ws;
     tb.v0 = (double*)(tb.c + n_samples);
     tb.dv = tb.v0 + n_samples;
-    tb.e = (long long*)(tb.dv + n_samples);
+    tb.dv32 = tb.dv + n_samples;
+    tb.e = (long long*)(tb.dv32 + n_samples);
     k_cia_intervals<<<(unsigned)((n_samples + 255) / 256), 256, 0, s>>>(A, cia->nu, cia->k, g, tb);
     const long long tiles = (long long)n_T * ((n + 32LL * ROX_CIA_GRUN - 1) / (32LL * ROX_CIA_GRUN));
     long long blocks = (tiles + ROX_CIA_GWARPS - 1) / ROX_CIA_GWARPS;
@@ -328,7 +332,7 @@ int cia_launch(const rox_cia* cia, const double* nodes, double nu_min, double dn
 
 extern "C" size_t rox_cia_workspace_size(int32_t n_blocks, int64_t n_samples) {
   if (n_blocks < 0 || n_samples < 0) return 0;
-  return sizeof(double) * (3 * (size_t)n_samples + (size_t)n_blocks);
+  return sizeof(double) * (4 * (size_t)n_samples + (size_t)n_blocks);
 }
 
 extern "C" int rox_cia_regrid(const rox_cia* cia, const rox_grid* grid, int n_T, const double* T_out, double* out,

@@ -127,7 +127,7 @@ def test_cia_arguments_rejected_on_host(lib):
     """CIA restructuring: every malformed layout is refused before anything reaches the GPU
     (the device pointers here are placeholders that are never dereferenced)."""
     L = lib.lib
-    assert L.rox_cia_workspace_size(2, 10) == 8 * (3 * 10 + 2)
+    assert L.rox_cia_workspace_size(2, 10) == 8 * (4 * 10 + 2)
 
     def call(T_block, offset, T_out, grid=(0.0, 1.0, 10), ws=256, ws_bytes=1 << 20, nodes=None):
         tb = (ctypes.c_double * max(1, len(T_block)))(*T_block)
