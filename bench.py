@@ -1192,32 +1192,36 @@ def run_cia(args):
 
 
 def run_autotune(args):
-    """Sweeps the launch configuration on one 1e8-line chunk of the large list and on the exomol
-    list, writes the cache (paper_2510_20870_gb300/tuning.json) and prints the results."""
+    """Sweeps the launch configuration on one 1e8-line chunk of the large list, on the exomol
+    list and on the batch list (1e8 lines; every eleventh of its 300 (P,T) points, so one candidate
+    takes seconds, with the same line density and the same mix of widths), writes the cache
+    (paper_2510_20870_gb300/tuning.json) and prints the results."""
     import torch
     import paper_2510_20870_gb300 as rox
     from paper_2510_20870_gb300 import autotune
     from rox_synth.device import make_lines_device
     out = {}
-    for cls, cid, n in (("large", 4, 100_000_000), ("exomol", 2, None)):
+    for cls, cid, n in (("large", 4, 100_000_000), ("exomol", 2, None), ("batch", 3, None)):
         w = rs.CONFIGS[cid]
         grid = rs.grid_of(w)
-        (P, T), = w.pts
+        pts = rs.pt_points(w)[::11]
+        P, T = [p for p, _ in pts], [t for _, t in pts]
         q = rs.q_table(w)
-        Qt, Qr = q_of(q, T), q_of(q, 296.0)
+        Qt, Qr = [q_of(q, t) for t in T], q_of(q, 296.0)
         n = n or w.n_lines
         raw = make_lines_device(w, 0, n)
         lines = {k: (torch.empty_like(v) if isinstance(v, torch.Tensor) else v) for k, v in raw.items()}
         sws = torch.empty(rox.rox_sort_workspace_size(n), dtype=torch.uint8, device="cuda")
         rox.rox_sort_lines(raw, lines, None, sws)
         del raw, sws
-        ws = torch.empty(rox.rox_xsec_workspace_size(n, grid, 1), dtype=torch.uint8, device="cuda")
-        sigma = torch.empty((1, grid[2]), dtype=torch.float32, device="cuda")
+        ws = torch.empty(rox.rox_xsec_workspace_size(n, grid, len(set(T))), dtype=torch.uint8, device="cuda")
+        sigma = torch.empty((len(pts), grid[2]), dtype=torch.float32, device="cuda")
 
         def step():
-            rox.rox_xsec_batch(lines, grid, [P], [T], [Qt], Qr, w.mass_amu, w.cutoff, sigma, ws, flags=rox.ROX_KAHAN)
-        res = autotune.sweep(step, reps=2 if cid == 4 else 5)
-        best = autotune.save(cls, res, note="%s: %d lines, one rox_xsec_batch call" % (w.name, n))
+            rox.rox_xsec_batch(lines, grid, P, T, Qt, Qr, w.mass_amu, w.cutoff, sigma, ws, flags=rox.ROX_KAHAN)
+        res = autotune.sweep(step, reps=5 if cid == 2 else (1 if cid == 3 else 2))
+        best = autotune.save(cls, res, note="%s: %d lines, %d (P,T) point(s), one rox_xsec_batch call" % (
+            w.name, n, len(pts)))
         out[autotune.key(cls)] = {"best": best, "results": [{"config": c, "ms": ms} for c, ms in res]}
         del lines, ws, sigma
         torch.cuda.empty_cache()
