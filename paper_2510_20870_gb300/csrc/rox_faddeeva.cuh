@@ -16,15 +16,17 @@
 //                      node x_c (step 1/8, nodes to 7.25). This form keeps relative accuracy
 //                      in the Gaussian tail near the real axis, where Re w is tiny next to
 //                      Im w.
-// The two core forms (rox_re_w_core) hold 9e-6 out to |z| = 7.1 for y < 0.5; the Voigt
-// kernel uses them directly in the |z| < 6.5 zone of lines with the Pade far form.
+// The two core forms (rox_re_w_core) hold 1.1e-5 out to |z| = 7.1 for y < 0.5 and 2e-6 for
+// 0.5 <= y <= 1.01; the Voigt kernel uses them directly in the |z| < 6.5 zones of lines with the
+// Pade far form (boundary 6.5^2 for y < 1.006).
 // The continued fraction truncations miss the exponentially small e^{-z^2} part of w,
 // which can matter just outside |z| = 6 when y is essentially zero; it is added there.
 //
 // The Voigt kernel's far zone (rox_re_w_far) uses one rational form in u = x^2 per line,
-// whose coefficients depend on y only: for y < 0.5 a [1/2] Pade approximant in 1/u of the
-// large-|x| expansion of Re w at fixed y, valid for s >= 6.5^2; otherwise the 2-level fraction,
-// valid for s >= 22^2.
+// whose coefficients depend on y only: for y < 0.75 and for 0.95 <= y < 11.5 a [1/2] Pade
+// approximant in 1/u of the large-|x| expansion of Re w at fixed y, valid for
+// s >= max(6.5^2, 42 y); otherwise (around its coefficients' pole at y = 0.866, and for large y)
+// the 2-level fraction, valid for s >= 22^2.
 #pragma once
 #include <math.h>
 
@@ -46,8 +48,11 @@
 #define ROX_S_CF3 100.0f     // 10^2
 #define ROX_S_CF5 36.0f      // 6^2
 #define ROX_Y_WEIDEMAN 0.1f
-#define ROX_S_PADE 42.25f    // 6.5^2: far-zone boundary of the per-line Pade form
-#define ROX_Y_PADE 0.5f      // the Pade form is used for y below this
+#define ROX_S_PADE 42.25f    // 6.5^2: the smallest far-zone boundary of the per-line Pade form
+#define ROX_Y_PADE 0.75f     // the Pade form is used for y below this ...
+#define ROX_Y_POLE_HI 0.95f  // ... and from here (its coefficients have a pole at y = 0.866) ...
+#define ROX_Y_PADE_MAX 11.5f // ... up to here, with the boundary s = max(6.5^2, 42 y)
+#define ROX_PADE_R2_PER_Y 42.0f
 
 ROX_FN float rox_rcp(float v) {
 #ifdef __CUDA_ARCH__
@@ -108,28 +113,33 @@ ROX_FN float rox_re_w_cf2(float x, float y) {
 
 // Far-zone form with per-line coefficients, in t = u + alpha (u = x^2):
 //   Re w ~ (y / sqrt(pi)) (t + kappa) / (t^2 + beta),   valid for s = u + y^2 >= r2.
-// For y < 0.5 the coefficients make (u + b)/(u^2 + c u + d) (alpha = c/2, kappa = b - c/2,
+// For the Pade ranges of y the coefficients make (u + b)/(u^2 + c u + d) (alpha = c/2, kappa = b - c/2,
 // beta = d - c^2/4) agree with the first four terms of the expansion of Re w(x + iy)
 // sqrt(pi)/y in powers of 1/u at fixed v = y^2, obtained from the asymptotic series
 // w ~ (i/sqrt(pi)) sum_n (2n-1)!!/2^n z^-(2n+1):
 //   1/u + (3/2 - v)/u^2 + (v^2 - 5v + 15/4)/u^3 + (-v^3 + 21v^2/2 - 105v/4 + 105/8)/u^4.
-// Max relative error against wofz 3.4e-6 for s >= 6.5^2, 1e-9 <= y < 0.5. The form lacks the
-// Gaussian part e^{-x^2} (below 4.5e-19 of the line peak there), which is why the relative
-// bound needs y >= 1e-9; for smaller y the absolute error stays below 4.5e-19 of the peak. The denominator has real roots at
-// u < 4.1 (|x| < 2.03), inside |z| < 6.5, where the form is never used. For y >= 0.5 (the approximant has a pole at
-// v = 3/4): the 2-level continued fraction, alpha = v - 1/2, beta = 2v, kappa = 1, s >= 22^2.
+// Max relative error against wofz 3.4e-6 for s >= max(6.5^2, 42 y), 1e-9 <= y < 0.75 and
+// 0.95 <= y < 11.5 (the boundary 42 y follows the smallest radius that holds that bound, found by
+// a scan of y against wofz; it grows with y because the expansion's coefficients grow like
+// powers of v). The form lacks the Gaussian part e^{-x^2} (below 4.5e-19 of the line peak
+// there), which is why the relative bound needs y >= 1e-9; for smaller y the absolute error stays
+// below 4.5e-19 of the peak. Real roots of the denominator exist only for y <= 1.5, at
+// t = sqrt(-beta) <= 4, far below t at the zone boundary (> 36): the form is never used there.
+// Between y = 0.75 and 0.95 the approximant's coefficients pass a pole (v = 3/4), and beyond
+// y = 11.5 its boundary would pass 22: there the 2-level continued fraction, alpha = v - 1/2,
+// beta = 2v, kappa = 1, s >= 22^2.
 struct rox_far {
   float alpha, beta, kappa, r2;
 };
 ROX_FN rox_far rox_far_coefs(float y) {
   rox_far f;
   const float v = y * y;
-  if (y < ROX_Y_PADE) {
-    const float q = rox_rcp(4.0f * v - 3.0f);       // in [-1/2, -1/3]
+  if (y < ROX_Y_PADE || (y >= ROX_Y_POLE_HI && y < ROX_Y_PADE_MAX)) {
+    const float q = rox_rcp(4.0f * v - 3.0f);       // |4v - 3| >= 0.61 on both ranges
     f.alpha = 0.5f * fmaf(v, fmaf(8.0f, v, -30.0f), 15.0f) * q;
     f.beta = 0.5f * fmaf(v, fmaf(v, fmaf(64.0f, v, -216.0f), 180.0f), -45.0f) * q * q;
     f.kappa = 3.0f * fmaf(-2.0f, v, 1.0f) * q;
-    f.r2 = ROX_S_PADE;
+    f.r2 = fmaxf(ROX_S_PADE, ROX_PADE_R2_PER_Y * y);
   } else {
     f.alpha = v - 0.5f;
     f.beta = 2.0f * v;

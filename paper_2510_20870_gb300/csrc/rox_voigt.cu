@@ -19,8 +19,9 @@
 // B = beta gamma_G^4, K = kappa gamma_G^2, i.e. 4 FMAs and one reciprocal; two lines share
 // one reciprocal (n1/d1 + n2/d2 = (n1 d2 + n2 d1)/(d1 d2)), so a pair costs 12 FP32
 // operations and one MUFU per point, three of them as paired (f32x2) instructions. The slow
-// zone is x^2 + y^2 < 6.5^2 for y < 0.5 (per-line Pade form) and < 22^2 otherwise (2-level
-// continued fraction), at least the precision margin.
+// zone is x^2 + y^2 < max(6.5^2, 42 y) for the lines with the per-line Pade form (y < 0.75 and
+// 0.95 <= y < 11.5) and < 22^2 for the others (2-level continued fraction), at least the
+// precision margin.
 // Lines are evaluated in two passes per batch. Pass 1 applies the far formula to every line at
 // every point of its window, in pairs; a line whose slow zone meets the span has t clamped to
 // the zone boundary, t = max(t, t_z), so inside the zone it adds the far form's (finite) value
@@ -258,7 +259,7 @@ __device__ __forceinline__ void edge_line(const PairTab& P, const LineTab& L, in
 // Pass 2 for the line in slot s, whose slow zone meets the span: at exactly the points where
 // pass 1 clamped t (t < t_z on the same rounded t, inside the window), the full FP32 Faddeeva
 // forms replace the far form's boundary value that pass 1 added there: + S V - cf.
-// A zone of |z| < 6.5 takes the core forms at every point (rox_re_w_core holds 9e-6 out to
+// A zone of |z| < 6.5 takes the core forms at every point (rox_re_w_core holds 1.1e-5 out to
 // |z| = 7.1); on a uniform grid the lanes then take consecutive points of the zone rather than
 // aligned 32-point sub-spans (fewer, fuller warp steps). Otherwise, per 32-point sub-span, one
 // form for all points where possible: the 3-level fraction if even the sub-span's point nearest

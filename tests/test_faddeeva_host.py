@@ -77,14 +77,20 @@ def host_far():
 
 
 def test_far_form_accuracy_outside_its_zone(host_far):
-    """The Voigt kernel's pair formula: the per-line Pade form (y < 0.5) from |z| = 6.5 outward
-    and the 2-level fraction (y >= 0.5) from |z| = 22 outward, against wofz."""
+    """The Voigt kernel's pair formula: the per-line Pade form (y < 0.75 and 0.95 <= y < 11.5)
+    from |z|^2 = max(6.5^2, 42 y) outward and the 2-level fraction (the other y) from |z| = 22
+    outward, against wofz."""
     far, r2 = host_far
     worst = {}
-    for y in np.concatenate([[0.0, 1e-12], np.logspace(-9, np.log10(0.4999), 120), [0.5, 0.7, 0.866, 1.0],
-                             np.logspace(0, 3, 40)]).astype(np.float32):
+    pade_ys = set()
+    for y in np.concatenate([[0.0, 1e-12], np.logspace(-9, np.log10(0.4999), 120),
+                             [0.5, 0.6, 0.7, 0.7499, 0.75, 0.8, 0.866, 0.9, 0.9499, 0.95, 1.0, 1.5, 11.49, 11.5],
+                             np.linspace(1.0, 11.4, 53), np.logspace(0, 3, 40)]).astype(np.float32):
         R2 = r2(float(y))
-        assert R2 == (42.25 if y < 0.5 else 484.0)
+        pade = y < 0.75 or 0.95 <= y < 11.5
+        assert R2 == (max(42.25, np.float32(42.0) * y) if pade else 484.0), (y, R2)
+        if pade:
+            pade_ys.add(float(y))
         x0 = np.sqrt(max(0.0, R2 - float(y) ** 2))
         x = np.concatenate([x0 + np.linspace(0, 2, 401), x0 + np.logspace(0.31, 5, 400)]).astype(np.float32)
         x = x[x.astype(np.float64) ** 2 + float(y) ** 2 >= R2]
@@ -100,8 +106,9 @@ def test_far_form_accuracy_outside_its_zone(host_far):
             rel = np.abs(got[m] - ref[m]) / ref[m]
             worst[float(y)] = rel.max()
         assert np.all(np.abs(got[~m]) < 2e-15)
-    pade = max(v for k, v in worst.items() if k < 0.5)
-    cf2 = max(v for k, v in worst.items() if k >= 0.5)
+    pade = max(v for k, v in worst.items() if k in pade_ys)
+    cf2 = max(v for k, v in worst.items() if k not in pade_ys)
+    print("far form: Pade worst %.2e, 2-level fraction worst %.2e" % (pade, cf2))
     assert pade < 6e-6, pade      # 3.4e-6 in exact arithmetic, plus FP32 rounding
     assert cf2 < 2e-5, cf2
 
@@ -121,14 +128,15 @@ def test_far_form_pade_reduces_to_series(host_far):
 
 def test_core_forms_to_radius_7():
     """rox_re_w_core (Dawson-Taylor for y < 0.1, Weideman above) stands alone in the Voigt
-    kernel's |z| < 6.5 zone of lines with the Pade far form (y < 0.5): it must hold out to
-    |z| = 7.1 there."""
+    kernel's |z| < 6.5 zone of lines with the Pade far form and the boundary 6.5^2 (y < 0.75 and
+    0.95 <= y < 1.006): it must hold out to |z| = 7.1 there."""
     import __graft_entry__
     lib = ctypes.CDLL(__graft_entry__._build_module().build_host_lib())
     f = lib.rox_host_re_w_core
     f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     worst = 0.0
-    for y in np.concatenate([[0.0, 1e-9], np.logspace(-7, np.log10(0.4999), 150)]):
+    for y in np.concatenate([[0.0, 1e-9], np.logspace(-7, np.log10(0.4999), 150), np.linspace(0.5, 0.75, 11),
+                             np.linspace(0.95, 1.01, 7)]):
         x = np.linspace(0, np.sqrt(max(0.0, 7.1 ** 2 - y * y)), 1500).astype(np.float32)
         yy = np.full_like(x, np.float32(y))
         out = np.empty_like(x)
