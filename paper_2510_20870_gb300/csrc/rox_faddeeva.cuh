@@ -23,10 +23,11 @@
 // which can matter just outside |z| = 6 when y is essentially zero; it is added there.
 //
 // The Voigt kernel's far zone (rox_re_w_far) uses one rational form in u = x^2 per line,
-// whose coefficients depend on y only: for y < 0.75 and for 0.95 <= y < 11.5 a [1/2] Pade
-// approximant in 1/u of the large-|x| expansion of Re w at fixed y, valid for
-// s >= max(6.5^2, 42 y); otherwise (around its coefficients' pole at y = 0.866, and for large y)
-// the 2-level fraction, valid for s >= 22^2.
+// whose coefficients depend on y only: for y < 11.5 a [1/2] Pade approximant in 1/u of the
+// large-|x| expansion of Re w at fixed y, valid for s >= 6.5^2 (y < 0.75),
+// 6.5^2 + 3.5 / |4 y^2 - 3| (0.75 <= y < 0.95, around its coefficients' pole at y = 0.866) or
+// max(6.5^2, 42 y) (0.95 <= y < 11.5); where that boundary would pass 22^2 (within 0.0012 of
+// the pole, and y >= 11.5) the 2-level fraction, valid for s >= 22^2.
 #pragma once
 #include <math.h>
 
@@ -49,10 +50,11 @@
 #define ROX_S_CF5 36.0f      // 6^2
 #define ROX_Y_WEIDEMAN 0.1f
 #define ROX_S_PADE 42.25f    // 6.5^2: the smallest far-zone boundary of the per-line Pade form
-#define ROX_Y_PADE 0.75f     // the Pade form is used for y below this ...
-#define ROX_Y_POLE_HI 0.95f  // ... and from here (its coefficients have a pole at y = 0.866) ...
-#define ROX_Y_PADE_MAX 11.5f // ... up to here, with the boundary s = max(6.5^2, 42 y)
+#define ROX_Y_PADE 0.75f     // the Pade form: boundary s = 6.5^2 for y below this,
+#define ROX_Y_POLE_HI 0.95f  // 6.5^2 + 3.5 / |4 y^2 - 3| up to here (its coefficients' pole is at y = 0.866),
+#define ROX_Y_PADE_MAX 11.5f // max(6.5^2, 42 y) up to here
 #define ROX_PADE_R2_PER_Y 42.0f
+#define ROX_PADE_R2_POLE 3.5f
 
 ROX_FN float rox_rcp(float v) {
 #ifdef __CUDA_ARCH__
@@ -118,28 +120,33 @@ ROX_FN float rox_re_w_cf2(float x, float y) {
 // sqrt(pi)/y in powers of 1/u at fixed v = y^2, obtained from the asymptotic series
 // w ~ (i/sqrt(pi)) sum_n (2n-1)!!/2^n z^-(2n+1):
 //   1/u + (3/2 - v)/u^2 + (v^2 - 5v + 15/4)/u^3 + (-v^3 + 21v^2/2 - 105v/4 + 105/8)/u^4.
-// Max relative error against wofz 3.4e-6 for s >= max(6.5^2, 42 y), 1e-9 <= y < 0.75 and
-// 0.95 <= y < 11.5 (the boundary 42 y follows the smallest radius that holds that bound, found by
-// a scan of y against wofz; it grows with y because the expansion's coefficients grow like
-// powers of v). The form lacks the Gaussian part e^{-x^2} (below 4.5e-19 of the line peak
+// Max relative error against wofz 3.4e-6 beyond those boundaries, for y >= 1e-9 (each boundary
+// rule covers the smallest radius that holds that bound, found by a scan of y against wofz: it
+// grows near the pole, where the coefficients diverge, and with y, because the expansion's
+// coefficients grow like powers of v). The form lacks the Gaussian part e^{-x^2} (below 4.5e-19 of the line peak
 // there), which is why the relative bound needs y >= 1e-9; for smaller y the absolute error stays
-// below 4.5e-19 of the peak. Real roots of the denominator exist only for y <= 1.5, at
-// t = sqrt(-beta) <= 4, far below t at the zone boundary (> 36): the form is never used there.
-// Between y = 0.75 and 0.95 the approximant's coefficients pass a pole (v = 3/4), and beyond
-// y = 11.5 its boundary would pass 22: there the 2-level continued fraction, alpha = v - 1/2,
-// beta = 2v, kappa = 1, s >= 22^2.
+// below 4.5e-19 of the peak. Real roots of the denominator (y <= 1.5 only, at
+// t = sqrt(-beta)) lie below t at the zone boundary for every y (the same scan): the form is
+// never used there.
+// Next to the pole (v = 3/4: |4v - 3| < 0.0079) and beyond y = 11.5 the boundary would pass 22:
+// there the 2-level continued fraction, alpha = v - 1/2, beta = 2v, kappa = 1, s >= 22^2.
 struct rox_far {
   float alpha, beta, kappa, r2;
 };
 ROX_FN rox_far rox_far_coefs(float y) {
   rox_far f;
   const float v = y * y;
-  if (y < ROX_Y_PADE || (y >= ROX_Y_POLE_HI && y < ROX_Y_PADE_MAX)) {
-    const float q = rox_rcp(4.0f * v - 3.0f);       // |4v - 3| >= 0.61 on both ranges
+  const float g = fmaf(4.0f, v, -3.0f);            // the coefficients' pole: g = 0
+  float r2 = ROX_S_FAR;
+  if (y < ROX_Y_PADE) r2 = ROX_S_PADE;
+  else if (y < ROX_Y_POLE_HI) r2 = ROX_S_PADE + ROX_PADE_R2_POLE * rox_rcp(fabsf(g));   // inf at the pole
+  else if (y < ROX_Y_PADE_MAX) r2 = fmaxf(ROX_S_PADE, ROX_PADE_R2_PER_Y * y);
+  if (r2 < ROX_S_FAR) {   // |g| >= 0.0079 here
+    const float q = rox_rcp(g);
     f.alpha = 0.5f * fmaf(v, fmaf(8.0f, v, -30.0f), 15.0f) * q;
     f.beta = 0.5f * fmaf(v, fmaf(v, fmaf(64.0f, v, -216.0f), 180.0f), -45.0f) * q * q;
     f.kappa = 3.0f * fmaf(-2.0f, v, 1.0f) * q;
-    f.r2 = fmaxf(ROX_S_PADE, ROX_PADE_R2_PER_Y * y);
+    f.r2 = r2;
   } else {
     f.alpha = v - 0.5f;
     f.beta = 2.0f * v;

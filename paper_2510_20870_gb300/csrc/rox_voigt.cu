@@ -19,9 +19,9 @@
 // B = beta gamma_G^4, K = kappa gamma_G^2, i.e. 4 FMAs and one reciprocal; two lines share
 // one reciprocal (n1/d1 + n2/d2 = (n1 d2 + n2 d1)/(d1 d2)), so a pair costs 12 FP32
 // operations and one MUFU per point, three of them as paired (f32x2) instructions. The slow
-// zone is x^2 + y^2 < max(6.5^2, 42 y) for the lines with the per-line Pade form (y < 0.75 and
-// 0.95 <= y < 11.5) and < 22^2 for the others (2-level continued fraction), at least the
-// precision margin.
+// zone is x^2 + y^2 < r^2(y) for the lines with the per-line Pade form (y < 11.5 except next to
+// its coefficients' pole at y = 0.866; r^2 from 6.5^2 to below 22^2, rox_far_coefs) and < 22^2
+// for the others (2-level continued fraction), at least the precision margin.
 // Lines are evaluated in two passes per batch. Pass 1 applies the far formula to every line at
 // every point of its window, in pairs; a line whose slow zone meets the span has t clamped to
 // the zone boundary, t = max(t, t_z), so inside the zone it adds the far form's (finite) value

@@ -77,19 +77,30 @@ def host_far():
 
 
 def test_far_form_accuracy_outside_its_zone(host_far):
-    """The Voigt kernel's pair formula: the per-line Pade form (y < 0.75 and 0.95 <= y < 11.5)
-    from |z|^2 = max(6.5^2, 42 y) outward and the 2-level fraction (the other y) from |z| = 22
-    outward, against wofz."""
+    """The Voigt kernel's pair formula, against wofz: the per-line Pade form from |z|^2 = 6.5^2
+    (y < 0.75), 6.5^2 + 3.5 / |4 y^2 - 3| (0.75 <= y < 0.95, around its coefficients' pole at
+    y = 0.866) and max(6.5^2, 42 y) (0.95 <= y < 11.5) outward; the 2-level fraction from |z| = 22
+    outward where the Pade boundary would pass 22 (next to the pole, and y >= 11.5)."""
     far, r2 = host_far
     worst = {}
     pade_ys = set()
     for y in np.concatenate([[0.0, 1e-12], np.logspace(-9, np.log10(0.4999), 120),
                              [0.5, 0.6, 0.7, 0.7499, 0.75, 0.8, 0.866, 0.9, 0.9499, 0.95, 1.0, 1.5, 11.49, 11.5],
+                             np.linspace(0.75, 0.95, 81), 0.8660254 + np.linspace(-0.004, 0.004, 33),
                              np.linspace(1.0, 11.4, 53), np.logspace(0, 3, 40)]).astype(np.float32):
         R2 = r2(float(y))
-        pade = y < 0.75 or 0.95 <= y < 11.5
-        assert R2 == (max(42.25, np.float32(42.0) * y) if pade else 484.0), (y, R2)
-        if pade:
+        if y < 0.75:
+            want = 42.25
+        elif y < 0.95:
+            g = abs(float(np.float32(4.0) * y * y - np.float32(3.0)))
+            want = 42.25 + 3.5 / g if g > 0 else np.inf
+        elif y < 11.5:
+            want = max(42.25, float(np.float32(42.0) * y))
+        else:
+            want = np.inf
+        want = want if want < 484.0 else 484.0
+        assert abs(R2 - want) <= 1e-5 * want, (y, R2, want)
+        if R2 < 484.0:
             pade_ys.add(float(y))
         x0 = np.sqrt(max(0.0, R2 - float(y) ** 2))
         x = np.concatenate([x0 + np.linspace(0, 2, 401), x0 + np.logspace(0.31, 5, 400)]).astype(np.float32)
