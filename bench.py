@@ -36,15 +36,15 @@ import rox_synth as rs  # noqa: E402
 
 FLOPS_PER_EVAL = 11.0   # far-wing pair formula: 10 FFMA + 2 FMUL per 2 evaluations (+ 1 MUFU rcp)
 # DRAM bytes per Voigt launch on the full exomol workload: ncu dram__bytes_read + write of the
-# 2e6-line case (151.0 MB + 43.4 MB, profiles/k_voigt_exomol_2e6lines.md), scaled by evaluations
+# 2e6-line case (151.3 MB + 43.4 MB, profiles/k_voigt_exomol_2e6lines.md), scaled by evaluations
 # (x5.0); most of the writes are L2 write-backs of the per-line constants k_line_params wrote
-VOIGT_TRAFFIC_BYTES = 9.717e8
+VOIGT_TRAFFIC_BYTES = 9.737e8
 # DRAM bytes of one k_cia_grid launch on the CIA workload (ncu dram__bytes_read + write,
 # profiles/k_cia_grid_40T_2970001pts.md; part of the 950 MB output is still in L2 at the end)
 CIA_TRAFFIC_BYTES = 8.955e8
 # DRAM bytes per evaluation of k_voigt on the large list: ncu dram__bytes_read + write on one
-# 1e7-line chunk of it (4.160 GB for 1.989e11 evaluations, profiles/k_voigt_large_1e7_chunk.md)
-VOIGT_TRAFFIC_LARGE = 4.1596e9 / 1.98948e11
+# 1e7-line chunk of it (4.170 GB for 1.989e11 evaluations, profiles/k_voigt_large_1e7_chunk.md)
+VOIGT_TRAFFIC_LARGE = 4.1697e9 / 1.98948e11
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "Voigt line-profile evals/s"
