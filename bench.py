@@ -1003,7 +1003,7 @@ def _sorted_device_lines(w, start, count, stream=None):
 
 
 def run_batch_config(args):
-    """Config 3: 1e8 lines, 15 P x 20 T = 300 cross-sections in one persistent launch (about 45 s
+    """Config 3: 1e8 lines, 15 P x 20 T = 300 cross-sections in one persistent launch (about 52 s
     a step on GB300, so not the default workload: the default K = 20, W = 5 would hold the GPU for
     about 20 minutes). Same keys as the default line; the end-to-end leg uploads the unsorted list
     from pinned memory, sorts it, computes the 300 cross-sections and reads the 3.56 GB back."""
